@@ -1,0 +1,355 @@
+"""Benchmark of the BDD Lagrange-dual hot path (DOGE-Train's Alg. 1 on GB300).
+
+One step = one dual iteration of generalized min-marginal averaging over the
+whole instance: forward sweep, S reduction, backward sweep (with the
+subproblem energies), S reduction and the FP64 per-instance lower bound.
+Metric: BDD-arc updates per second (2 sweeps x 2 arcs per node per
+iteration), with the HBM roofline of the sweep kernel beside it.
+
+Default workload: the tracking-like flow instance (500 frames x 2,000
+detections, ~6M variables, ~3M constraints), the largest single-GPU
+configuration.  Inputs are seeded synthetic data (the paper's datasets are
+not available).
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Multi-GPU: every rank solves its own copy of the instance (independent
+problems, no collective); value = arc updates of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "BDD-arc updates/s per dual iteration (forward+backward sweep)"
+UNIT = "arc-updates/s"
+WORKLOADS = {
+    "tracking_500x2000": lambda: workloads.tracking(),
+    "matching_quadratic_200": lambda: workloads.matching_quadratic(),
+    "independent_set_10k": lambda: workloads.independent_set(),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def _profile_traffic(kernel_key: str, src_sha: str):
+    """DRAM bytes per launch recorded by an ncu capture (profiles/*.md), or
+    None when absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_key}.md")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("source_sha") != src_sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels_sweep.cu", "sweep.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2205_11638_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_oracle_rate(budget_s: float = 15.0, frames: int = 50):
+    """The FP64 oracle (single-threaded C++) on a 50-frame slice of the
+    tracking workload: arc updates per second over whole iterations."""
+    import oracle
+    prob = workloads.tracking(frames=frames, dets=2000)
+    O = oracle.Oracle(prob)
+    lam, M = O.init_lambda()
+    arcs = 4 * O.num_nodes
+    t0 = time.perf_counter()
+    its = 0
+    while True:
+        lam, M = O.iterate(lam, M, 0.5, None, 1)
+        its += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": arcs * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"tracking {frames} frames x 2000 detections ({O.num_slots} slots, {O.num_nodes} nodes), "
+                      f"{its} iterations in {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    frames = 50
+    prob = workloads.tracking(frames=frames, dets=2000)
+    O = oracle.Oracle(prob)
+    lam, M = O.init_lambda()
+    arcs = 4 * O.num_nodes
+    for _ in range(args.warmup):
+        lam, M = O.iterate(lam, M, 0.5, None, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lam, M = O.iterate(lam, M, 0.5, None, 1)
+    dt = time.perf_counter() - t0
+    val = arcs * args.steps / dt
+    sample = f"tracking {frames} frames x 2000 detections ({O.num_slots} slots), one oracle iteration per step"
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "sample": sample},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2205_11638_gb300 import build, solver
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    prob = WORKLOADS[args.workload]()
+    t0 = time.perf_counter()
+    plan = solver.plan(prob, block_threads=args.threads, tile_nodes=args.tile_nodes, tile_slots=args.tile_slots)
+    A = plan.bind()
+    plan_s = time.perf_counter() - t0
+    st = A.stats
+    Nv, Nl, n = st.sizes.num_nodes, st.sizes.num_lambda, st.sizes.n
+    arcs_per_iter = 4 * Nv
+    stream = torch.cuda.current_stream()
+    lam, M = A.init_lambda()
+    lb_out = torch.zeros(A.num_inst, dtype=torch.float64, device=A.device)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        A.sweep(lam, M, forward=True)
+        if ev is not None:
+            ev[1].record(stream)
+        A.sum_M(M)
+        if ev is not None:
+            ev[2].record(stream)
+        A.sweep(lam, M, forward=False, energy=True)
+        if ev is not None:
+            ev[3].record(stream)
+        A.sum_M(M)
+        A.bound_from_energies(lb_out)
+        if ev is not None:
+            ev[4].record(stream)
+
+    A.sum_M(M)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    for k in range(args.steps):
+        step(evs[k])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    t_fwd = [e[0].elapsed_time(e[1]) for e in evs]
+    t_red = [e[1].elapsed_time(e[2]) for e in evs]
+    t_bwd = [e[2].elapsed_time(e[3]) for e in evs]
+    t_tail = [e[3].elapsed_time(e[4]) for e in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][4])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=A.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t[0])
+    ms_per_step = total_ms / args.steps
+    value = arcs_per_iter * args.steps * ws / (total_ms * 1e-3)
+    lb_final = float(lb_out.sum())
+
+    # roofline of the dominant kernel (the sweep; forward and backward have
+    # the same algorithmic bytes): 16 B per node + 16 B per slot per sweep
+    sweep_bytes = 16.0 * Nv + 16.0 * Nl
+    sweep_ms = statistics.mean(t_fwd + t_bwd)
+    peak, peak_src = _peaks()
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    src_sha = _kernel_source_sha()
+    traffic = _profile_traffic(f"sweep_{args.workload}", src_sha)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": peak_src, "kernel": "k_sweep (forward and backward)",
+            "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": sweep_ms,
+            "iteration_algorithmic_bytes": st.bytes_per_iter,
+            "iteration_frac": st.bytes_per_iter / (ms_per_step * 1e-3) / 1e9 / peak,
+            "kernel_source_sha": src_sha}
+    shares = {"k_sweep_fwd": sum(t_fwd), "k_reduce_S": sum(t_red) + 0.0, "k_sweep_bwd": sum(t_bwd),
+              "k_reduce_S+k_lb": sum(t_tail)}
+    tot = sum(shares.values())
+    shares = {k: v / tot for k, v in shares.items()}
+
+    # end to end through the public API with host buffers: every step copies
+    # (lambda, M) from pinned host memory, runs one iteration with its bound
+    # and reads (lambda, M, bound) back
+    e2e = None
+    if not args.no_e2e:
+        h_lam = lam.detach().cpu().pin_memory()
+        h_M = M.detach().cpu().pin_memory()
+        h_lb = torch.zeros(A.num_inst, dtype=torch.float64).pin_memory()
+        d_lam, d_M = torch.empty_like(lam), torch.empty_like(M)
+        ke = min(args.steps, 10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            d_lam.copy_(h_lam, non_blocking=True)
+            d_M.copy_(h_M, non_blocking=True)
+            lbt = A.iterate(d_lam, d_M, iters=1, lb=True)
+            h_lam.copy_(d_lam, non_blocking=True)
+            h_M.copy_(d_M, non_blocking=True)
+            h_lb.copy_(lbt, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([e_ms], device=A.device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t[0])
+        nb = 2 * A.num_slots * 4
+        e2e = {"value": arcs_per_iter * ke * ws / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8 * A.num_inst,
+               "ms_per_step": e_ms / ke, "steps": ke}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = _cpu_oracle_rate(args.cpu_budget)
+
+    launches_per_step = 6  # fwd sweep, S, bwd sweep, S, lb partial, lb final
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "n_vars": int(n), "constraints": int(st.sizes.m),
+                      "N_lambda": int(Nl), "N_v": int(Nv), "arcs_per_iteration": int(arcs_per_iter),
+                      "tiles": int(st.sizes.num_tiles), "block_threads": args.threads or 256,
+                      "l2": f"inputs larger than L2 (arena {st.sizes.arena_bytes / 1e6:.0f} MB + state "
+                            f"{8 * A.num_slots / 1e6:.0f} MB)", "plan_bind_s": round(plan_s, 2),
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+           "roofline": roof, "kernel_shares": shares, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+           "gpu_launches": launches_per_step * args.steps, "lower_bound_after_run": lb_final}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tracking_500x2000", choices=sorted(WORKLOADS))
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tile-nodes", type=int, default=0)
+    ap.add_argument("--tile-slots", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,238 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) BDD Lagrange-dual solver.
+ *
+ * The solver is the data-parallel hot path of DOGE-Train (Abbas & Swoboda,
+ * arXiv 2205.11638): the Lagrange decomposition of a binary program
+ * (Def. 1, Def. 2, Sec. 3.1) with one BDD per constraint (App. B), optimised
+ * by generalized min-marginal averaging (Alg. 1, Sec. 3.2) and differentiated
+ * by Alg. 2 (Sec. 3.3).
+ *
+ * Conventions
+ *  - Every call returns a dg_status; dg_last_error() gives a thread-local
+ *    message for the last failing call of the calling thread.  No C++
+ *    exception crosses this boundary.
+ *  - Device calls are ordered on the caller's cudaStream_t (passed as void*;
+ *    NULL is the legacy default stream).  They never synchronise the device,
+ *    except dg_bind (which waits for its one host-to-device upload).
+ *  - Memory is owned by the caller.  dg_plan computes byte sizes; the caller
+ *    allocates the arena and the state vectors (e.g. with torch) and passes
+ *    device pointers.  The library allocates no device memory, except the
+ *    CUDA graph objects of dg_graph_create.
+ *  - "Arena order": state vectors (lambda, M, omega, alpha, gradients) are
+ *    float32 arrays of dg_sizes.num_slots entries in the order of the arena
+ *    (tiles of BDDs, hop-major inside a tile, padded).  dg_slot_map gives the
+ *    CSR position of every arena slot; padding slots map to -1 and are kept
+ *    at 0 by every call.
+ *  - Status codes: DG_EINVAL for malformed input, DG_EINFEASIBLE when a row
+ *    has no feasible assignment, DG_EFORCED when a row fixes one of its
+ *    variables (min-marginal of one value infinite; presolve is the caller's
+ *    job), DG_ECUDA for a failing CUDA call, DG_ESTATE for a call on an
+ *    unbound arena or with mismatched sizes.
+ */
+#ifndef DG_H_
+#define DG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dg_status {
+  DG_OK = 0,
+  DG_EINVAL = 1,
+  DG_ENOMEM = 2,
+  DG_ECUDA = 3,
+  DG_EINFEASIBLE = 4,
+  DG_EFORCED = 5,
+  DG_ETIMEOUT = 6,
+  DG_ESTATE = 7
+} dg_status;
+
+/* Constraint rows of one or several binary programs (Def. 1).  Row j is
+ * sum_{s in [row_ptr[j], row_ptr[j+1])} coef[s] * x_{col[s]}  (sense)  rhs[j]
+ * with sense 0 '<=', 1 '>=', 2 '='; columns strictly ascending within a row;
+ * integer coefficients.  c holds the objective (float64[n]).  A batch of
+ * independent instances is one problem whose rows and variables are grouped:
+ * instance k owns rows [inst_row_ptr[k], inst_row_ptr[k+1]) and variables
+ * [inst_var_ptr[k], inst_var_ptr[k+1]); with num_inst <= 1 both pointers may
+ * be NULL.  All pointers are host pointers borrowed for the call only. */
+typedef struct dg_rows {
+  int32_t num_inst;
+  const int64_t* inst_row_ptr;
+  const int32_t* inst_var_ptr;
+  int32_t n;
+  int64_t m;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int32_t* coef;
+  const int8_t* sense;
+  const int32_t* rhs;
+  const double* c;
+} dg_rows;
+
+/* Options (zero-initialise, then set what you need; 0 selects the default). */
+typedef struct dg_options {
+  int32_t tile_nodes;    /* node budget of one tile, multiple of 32 (default 2048) */
+  int32_t tile_slots;    /* slot budget of one tile (default 1024) */
+  int32_t block_threads; /* threads per CTA of the sweep kernels (default 256) */
+  int32_t renorm_every;  /* FP64 re-projection of lambda onto sum_j(lambda+M)=c
+                            every k iterations (0 = never) */
+  float omega;           /* damping of mode 0 (default 0.5 when 0) */
+  int32_t num_threads;   /* host threads for dg_plan (0 = hardware concurrency) */
+  int32_t reserved[8];
+} dg_options;
+
+typedef struct dg_sizes {
+  size_t arena_bytes;    /* device bytes dg_bind needs */
+  int64_t num_slots;     /* length of arena-order state vectors (padded) */
+  int64_t num_lambda;    /* real slots N_lambda = #(i,j) pairs */
+  int64_t num_nodes;     /* real BDD nodes N_v (terminals excluded) */
+  int64_t num_nodes_padded;
+  int32_t n;             /* variables */
+  int64_t m;             /* rows = BDDs */
+  int32_t num_inst;
+  int32_t num_tiles;
+  int32_t max_hops;      /* u = longest BDD */
+  int32_t max_width;     /* widest BDD level */
+  size_t smem_bytes;     /* dynamic shared memory of the largest tile */
+} dg_sizes;
+
+typedef struct dg_stats {
+  dg_sizes sizes;
+  int64_t num_arcs;             /* 2 * num_nodes */
+  double bytes_per_iter;        /* algorithmic bytes of one plain iteration:
+                                   32*N_v + 48*N_lambda + 16*n */
+  double actual_bytes_per_iter; /* bytes the kernels of this layout move per
+                                   plain iteration (16-bit child indices,
+                                   recomputed path costs) */
+  int64_t hop_histogram[64];    /* BDDs by hop count (last bin: >= 63) */
+} dg_stats;
+
+typedef struct dg_plan_s dg_plan_t;
+typedef struct dg_arena_s dg_arena;
+typedef struct dg_graph_s dg_graph_t;
+
+const char* dg_last_error(void);
+
+/* --- build (two phases: host plan, device bind) -------------------------- */
+
+/* Builds one canonical quasi-reduced BDD per row (App. B: every r-T path
+ * meets one node per variable, variables in ascending id order, nodes of a
+ * level ordered by (lo rank, hi rank) with bottom=-2 < top=-1) and packs the
+ * BDDs into tiles (hop-major structure-of-arrays).  Host only.  On success
+ * *out owns the host layout; sizes receives the device byte counts. */
+dg_status dg_plan(const dg_rows* rows, const dg_options* opts, dg_plan_t** out, dg_sizes* sizes);
+
+/* Same call under the name of the builder stage; identical to dg_plan. */
+dg_status dg_build(const dg_rows* rows, const dg_options* opts, dg_plan_t** out, dg_sizes* sizes);
+
+/* Uploads the plan into caller memory arena_dev (>= sizes.arena_bytes, 256-B
+ * aligned) on stream and waits for it.  The arena borrows arena_dev until
+ * dg_destroy.  The plan may be freed afterwards. */
+dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, void* stream, dg_arena** out);
+
+void dg_plan_free(dg_plan_t* plan);
+void dg_destroy(dg_arena* arena);
+
+dg_status dg_get_sizes(const dg_plan_t* plan, dg_sizes* sizes);
+dg_status dg_get_stats(const dg_arena* arena, dg_stats* stats);
+
+/* slot_to_csr[q] = CSR position (row_ptr[j] + h) of arena slot q, or -1 for
+ * padding (host array of num_slots entries). */
+dg_status dg_slot_map(const dg_plan_t* plan, int64_t* slot_to_csr);
+
+/* Structure of the BDD of row j as built (for bit-exact checks):
+ * level_start (k+1 ints), lo and hi (one per node; ranks on the next level,
+ * -2 bottom, -1 top).  *num_nodes receives the node count; pass NULL arrays
+ * to query it. */
+dg_status dg_bdd_export(const dg_plan_t* plan, int64_t j, int32_t* level_start, int32_t* lo, int32_t* hi,
+                        int32_t* num_nodes);
+
+/* --- solver (device pointers, arena order, float32) ---------------------- */
+
+/* Initial state (reading of Alg. 1's input): lambda_ij = c_i / |J_i|, M = 0. */
+dg_status dg_init_lambda(dg_arena* arena, void* stream, float* lam, float* M);
+
+/* Runs `iters` iterations of Alg. 1 in place on (lam, M): each is a forward
+ * sweep over the blocks B_1..B_u and a backward sweep B_u..B_1; every block
+ * computes the min-marginal differences through shortest paths (App. B) and
+ * applies BlockUpdate
+ *   M_ij      <- omega_ij (m1_ij - m0_ij)
+ *   lambda_ij <- lambda_ij - M_ij + alpha_ij * S_i,  S_i = sum_{k in J_i} M_ik
+ * with S_i a snapshot taken at the start of each sweep.
+ * mode 0: omega = opts->omega (scalar, 0.5 if 0), alpha_ij = 1/|J_i| (the
+ *         special case of the remark in Sec. 3.2); omega/alpha may be NULL.
+ * mode 1: per-slot arrays omega (in [0,1]) and alpha (>= 0, summing to 1 over
+ *         J_i).
+ * lb_out (nullable, float64[num_inst]) receives the lower bound after the
+ * last iteration: sum_j E^j(lambda) + sum_i min(0, S_i) (+ min(0, c_i) for
+ * variables in no row). */
+dg_status dg_iterate(dg_arena* arena, void* stream, float* lam, float* M, const float* omega, const float* alpha,
+                     int32_t mode, int32_t iters, double* lb_out, const dg_options* opts);
+
+/* The building blocks dg_iterate chains, for custom schedules and per-kernel
+ * timing.  dg_sum_M stores the snapshot S_i = sum_{j in J_i} M_ij inside the
+ * arena (with renorm != 0 it also re-projects lam onto
+ * sum_j (lambda_ij + M_ij) = c_i in FP64, weights as in mode).  dg_sweep runs
+ * one sweep of Alg. 1 (forward != 0: blocks B_1..B_u, else B_u..B_1) with
+ * that snapshot; with want_energy (backward sweeps only) it also stores
+ * E^j(lambda) of every row in the arena.  dg_bound_from_energies writes the
+ * per-instance lower bound from the stored E and S (float64[num_inst]).
+ * dg_iterate(iters) = dg_sum_M, then per iteration: dg_sweep(forward),
+ * dg_sum_M, dg_sweep(backward), dg_sum_M. */
+dg_status dg_sum_M(dg_arena* arena, void* stream, const float* M, float* lam, const float* alpha, int32_t mode,
+                   int32_t renorm);
+dg_status dg_sweep(dg_arena* arena, void* stream, float* lam, float* M, const float* omega, const float* alpha,
+                   int32_t mode, int32_t forward, int32_t want_energy, const dg_options* opts);
+dg_status dg_bound_from_energies(dg_arena* arena, void* stream, double* lb_out);
+
+/* Min-marginals m0, m1 of every slot under lam (no update): for slot (i,j),
+ * m^beta = min over x in X_j with x_i = beta of <lambda_.j, x>. */
+dg_status dg_min_marginals(dg_arena* arena, void* stream, const float* lam, float* m0, float* m1);
+
+/* Lower bound of (lam, M): lb_per_inst (float64[num_inst]) and, if not NULL,
+ * E_per_row (float32[m], original row order) = E^j(lambda_.j). */
+dg_status dg_lower_bound(dg_arena* arena, void* stream, const float* lam, const float* M, double* lb_per_inst,
+                         float* E_per_row);
+
+/* Gradient of the lower bound (eq. 3 plus the unary term) at (lam, M):
+ * g_lam = minimising assignment of every BDD (0-arc on ties),
+ * g_M_ij = [S_i < 0]. */
+dg_status dg_lb_seed(dg_arena* arena, void* stream, const float* lam, const float* M, float* g_lam, float* g_M);
+
+/* --- adjoint (Alg. 2) ----------------------------------------------------- */
+
+/* Device workspace dg_backward needs for `iters` iterations with a
+ * checkpoint every `ckpt_every` iterations. */
+size_t dg_backward_workspace_bytes(const dg_arena* arena, int32_t iters, int32_t ckpt_every);
+
+/* Backpropagation through `iters` iterations of dg_iterate started from
+ * (lam0, M0).  Seeds g_lam_T, g_M_T are the gradients of the loss with
+ * respect to the final (lam, M).  Outputs g_lam0, g_M0, g_omega, g_alpha
+ * (arena order; g_omega / g_alpha accumulate over all blocks as in Alg. 2,
+ * for mode 0 they are the gradients of the per-slot values the scalar
+ * expands to).  The forward pass is recomputed from checkpoints of (lam, M)
+ * kept every ckpt_every iterations in workspace. */
+dg_status dg_backward(dg_arena* arena, void* stream, const float* lam0, const float* M0, const float* omega,
+                      const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
+                      const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,
+                      void* workspace, size_t ws_bytes, const dg_options* opts);
+
+/* --- CUDA graph of the iteration loop ------------------------------------ */
+
+/* Captures `iters` iterations of dg_iterate (same arguments) into a CUDA
+ * graph; dg_graph_replay launches it on stream.  Pointers are baked in. */
+dg_status dg_graph_create(dg_arena* arena, void* stream, float* lam, float* M, const float* omega, const float* alpha,
+                          int32_t mode, int32_t iters, double* lb_out, const dg_options* opts, dg_graph_t** out);
+dg_status dg_graph_replay(dg_graph_t* g, void* stream);
+void dg_graph_destroy(dg_graph_t* g);
+
+/* Number of kernel launches one dg_iterate call with these arguments issues. */
+int32_t dg_iterate_launches(const dg_arena* arena, int32_t iters, int32_t want_lb, const dg_options* opts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H_ */

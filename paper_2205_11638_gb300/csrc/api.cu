@@ -1,0 +1,456 @@
+// api.cu -- the C ABI of libdg (declared in include/dg.h): status codes,
+// two-phase build (host plan, device bind), the solver calls, the CUDA graph
+// of the iteration loop.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "kernels.h"
+
+namespace dg {
+
+static thread_local std::string g_err;
+
+dg_status fail(dg_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+void clear_error() { g_err.clear(); }
+
+static dg_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(DG_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+struct dg_arena_s {
+  DevArena dev{};
+  dg_sizes sizes{};
+  dg_stats stats{};
+  size_t smem_sweep = 0, smem_adjoint = 0;
+  int device = 0;
+  int max_tile_rows = 0, max_tile_slots = 0, max_tile_hops = 0;
+};
+
+struct dg_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int threads_of(const dg_options* o) {
+  int t = o && o->block_threads > 0 ? o->block_threads : 256;
+  t = (t + 31) / 32 * 32;
+  return t < 32 ? 32 : (t > 512 ? 512 : t);
+}
+float omega_of(const dg_options* o) { return o && o->omega > 0.f ? o->omega : 0.5f; }
+
+dg_status check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  return DG_OK;
+}
+
+// Enqueues `iters` iterations (forward sweep, S, backward sweep, S per
+// iteration) on st.  The first S reduction makes the snapshot of the
+// incoming M.
+dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, const float* omega, const float* alpha,
+                          int mode, int iters, double* lb_out, const dg_options* opts) {
+  const DevArena& A = ar->dev;
+  const int threads = threads_of(opts);
+  const int renorm = opts ? opts->renorm_every : 0;
+  SweepArgs a{};
+  a.lam = lam;
+  a.M = M;
+  a.omega = omega;
+  a.alpha = alpha;
+  a.omega0 = omega_of(opts);
+  a.mode = mode;
+  launch_reduce_S(A, M, lam, alpha, mode, false, st);
+  for (int it = 0; it < iters; ++it) {
+    a.E = nullptr;
+    launch_sweep(kFwd, A, a, threads, ar->smem_sweep, st);
+    launch_reduce_S(A, M, lam, alpha, mode, false, st);
+    if (lb_out && it == iters - 1) a.E = A.E;
+    launch_sweep(kBwd, A, a, threads, ar->smem_sweep, st);
+    const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
+    launch_reduce_S(A, M, lam, alpha, mode, rn, st);
+  }
+  if (lb_out) {
+    if (iters == 0) {
+      SweepArgs e{};
+      e.lam = lam;
+      e.E = A.E;
+      launch_sweep(kEnergy, A, e, threads, ar->smem_sweep, st);
+    }
+    launch_lower_bound(A, lb_out, st);
+  }
+  return check_launch("dg_iterate");
+}
+
+dg_status check_state(const dg_arena* ar) {
+  if (!ar) return fail(DG_ESTATE, "null arena");
+  return DG_OK;
+}
+
+// Arena-order vectors are read and written as float4: 16-byte alignment.
+bool aligned16(const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+dg_status check_vectors(const char* where, const void* a, const void* b, const void* c = nullptr,
+                        const void* d = nullptr) {
+  if (!aligned16(a) || !aligned16(b) || !aligned16(c) || !aligned16(d))
+    return fail(DG_EINVAL, std::string(where) + ": state vectors must be 16-byte aligned");
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+dg_status dg_plan(const dg_rows* rows, const dg_options* opts, dg_plan_t** out, dg_sizes* sizes) {
+  clear_error();
+  if (!out) return fail(DG_EINVAL, "dg_plan: null out");
+  *out = nullptr;
+  dg_plan_t* p = nullptr;
+  try {
+    p = new dg_plan_t();
+    dg_status st = build_plan(rows, opts, p->p);
+    if (st != DG_OK) {
+      delete p;
+      return st;
+    }
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return fail(DG_ENOMEM, "dg_plan: host allocation failed");
+  } catch (const std::exception& e) {
+    delete p;
+    return fail(DG_EINVAL, std::string("dg_plan: ") + e.what());
+  }
+  if (p->p.smem_sweep > 227 * 1024 || p->p.smem_adjoint > 227 * 1024) {
+    // a single BDD larger than one CTA's shared memory
+    delete p;
+    return fail(DG_EINVAL, "dg_plan: a BDD does not fit one tile's shared memory");
+  }
+  if (sizes) *sizes = p->p.sizes;
+  *out = p;
+  return DG_OK;
+}
+
+dg_status dg_build(const dg_rows* rows, const dg_options* opts, dg_plan_t** out, dg_sizes* sizes) {
+  return dg_plan(rows, opts, out, sizes);
+}
+
+void dg_plan_free(dg_plan_t* plan) { delete plan; }
+
+dg_status dg_get_sizes(const dg_plan_t* plan, dg_sizes* sizes) {
+  if (!plan || !sizes) return fail(DG_EINVAL, "dg_get_sizes: null argument");
+  *sizes = plan->p.sizes;
+  return DG_OK;
+}
+
+dg_status dg_slot_map(const dg_plan_t* plan, int64_t* out) {
+  if (!plan || !out) return fail(DG_EINVAL, "dg_slot_map: null argument");
+  std::memcpy(out, plan->p.slot_to_csr.data(), plan->p.slot_to_csr.size() * sizeof(int64_t));
+  return DG_OK;
+}
+
+dg_status dg_bdd_export(const dg_plan_t* plan, int64_t j, int32_t* level_start, int32_t* lo, int32_t* hi,
+                        int32_t* num_nodes) {
+  if (!plan) return fail(DG_EINVAL, "dg_bdd_export: null plan");
+  const Plan& P = plan->p;
+  if (j < 0 || j >= P.sizes.m) return fail(DG_EINVAL, "dg_bdd_export: row out of range");
+  const int64_t nb = P.node_ptr[j], ne = P.node_ptr[j + 1];
+  if (num_nodes) *num_nodes = (int32_t)(ne - nb);
+  if (!level_start || !lo || !hi) return DG_OK;
+  // level widths from the tile layout are not kept; recount from the child
+  // ranks: level h+1 has as many nodes as the largest rank referenced + 1,
+  // and every level's nodes are contiguous in node order.
+  const int k = (int)(P.row_ptr[j + 1] - P.row_ptr[j]);
+  int pos = 0;
+  level_start[0] = 0;
+  int width = 1;  // root level
+  for (int h = 0; h < k; ++h) {
+    level_start[h + 1] = pos + width;
+    int next = 0;
+    for (int r = 0; r < width; ++r) {
+      lo[pos + r] = P.lo8[nb + pos + r];
+      hi[pos + r] = P.hi8[nb + pos + r];
+      next = std::max(next, std::max((int)lo[pos + r], (int)hi[pos + r]) + 1);
+    }
+    pos += width;
+    width = next;
+  }
+  return DG_OK;
+}
+
+dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, void* stream, dg_arena** out) {
+  clear_error();
+  if (!plan || !out) return fail(DG_EINVAL, "dg_bind: null argument");
+  *out = nullptr;
+  const Plan& P = plan->p;
+  if (!arena_dev || arena_bytes < P.off.total) return fail(DG_EINVAL, "dg_bind: arena buffer too small");
+  if (((uintptr_t)arena_dev & 255u) != 0) return fail(DG_EINVAL, "dg_bind: arena buffer must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  // host image of everything up to the scratch area
+  const size_t image = P.off.S;
+  std::vector<unsigned char> h(image, 0);
+  auto cp = [&](size_t off, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(h.data() + off, src, bytes);
+  };
+  cp(P.off.tiles, P.tiles.data(), P.tiles.size() * sizeof(Tile));
+  cp(P.off.hoptab, P.hoptab.data(), P.hoptab.size() * 4);
+  cp(P.off.rows, P.rows.data(), P.rows.size() * sizeof(RowMeta));
+  cp(P.off.lohi, P.lohi.data(), P.lohi.size() * 4);
+  cp(P.off.slot_var, P.slot_var.data(), P.slot_var.size() * 4);
+  cp(P.off.slot_row, P.slot_row.data(), P.slot_row.size() * 4);
+  cp(P.off.var_ptr, P.var_ptr.data(), P.var_ptr.size() * 4);
+  cp(P.off.var_slots, P.var_slots.data(), P.var_slots.size() * 4);
+  cp(P.off.c, P.c.data(), P.c.size() * 8);
+  cp(P.off.invdeg, P.invdeg.data(), P.invdeg.size() * 4);
+  cp(P.off.inst_row_ptr, P.inst_row_ptr.data(), P.inst_row_ptr.size() * 8);
+  cp(P.off.inst_var_ptr, P.inst_var_ptr.data(), P.inst_var_ptr.size() * 4);
+  cp(P.off.lb_chunks, P.lb_chunks.data(), P.lb_chunks.size() * 4);
+  cp(P.off.inst_chunk_ptr, P.inst_chunk_ptr.data(), P.inst_chunk_ptr.size() * 4);
+  cudaError_t e = cudaMemcpyAsync(arena_dev, h.data(), image, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)arena_dev + P.off.S, 0, P.off.total - P.off.S, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_bind upload");
+  {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "dg_bind: device attribute");
+    if ((size_t)optin < P.smem_sweep) return fail(DG_EINVAL, "dg_bind: tiles need more shared memory than a CTA has");
+    e = set_sweep_smem_limit((size_t)optin);  // same limit for every arena of the process
+    if (e != cudaSuccess) return cuda_fail(e, "dg_bind: shared-memory limit");
+  }
+  dg_arena* ar = new dg_arena();
+  cudaGetDevice(&ar->device);
+  char* b = (char*)arena_dev;
+  DevArena& A = ar->dev;
+  A.tiles = (const Tile*)(b + P.off.tiles);
+  A.hoptab = (const uint32_t*)(b + P.off.hoptab);
+  A.rows = (const RowMeta*)(b + P.off.rows);
+  A.lohi = (const uint32_t*)(b + P.off.lohi);
+  A.slot_var = (const int32_t*)(b + P.off.slot_var);
+  A.slot_row = (const int32_t*)(b + P.off.slot_row);
+  A.var_ptr = (const int32_t*)(b + P.off.var_ptr);
+  A.var_slots = (const int32_t*)(b + P.off.var_slots);
+  A.c = (const double*)(b + P.off.c);
+  A.invdeg = (const float*)(b + P.off.invdeg);
+  A.inst_row_ptr = (const int64_t*)(b + P.off.inst_row_ptr);
+  A.inst_var_ptr = (const int32_t*)(b + P.off.inst_var_ptr);
+  A.lb_chunks = (const int4*)(b + P.off.lb_chunks);
+  A.inst_chunk_ptr = (const int32_t*)(b + P.off.inst_chunk_ptr);
+  A.S = (float*)(b + P.off.S);
+  A.E = (float*)(b + P.off.E);
+  A.lb_part = (double*)(b + P.off.lb_part);
+  A.n = P.sizes.n;
+  A.num_inst = P.sizes.num_inst;
+  A.m = P.sizes.m;
+  A.num_slots = P.sizes.num_slots;
+  A.num_tiles = P.sizes.num_tiles;
+  A.num_lb_chunks = (int32_t)(P.lb_chunks.size() / 4);
+  ar->sizes = P.sizes;
+  ar->smem_sweep = P.smem_sweep;
+  ar->smem_adjoint = P.smem_adjoint;
+  ar->max_tile_rows = P.max_tile_rows;
+  ar->max_tile_slots = P.max_tile_slots;
+  ar->max_tile_hops = P.max_tile_hops;
+  dg_stats& S = ar->stats;
+  S.sizes = P.sizes;
+  S.num_arcs = 2 * P.sizes.num_nodes;
+  const double Nv = (double)P.sizes.num_nodes, Nl = (double)P.sizes.num_lambda, n = (double)P.sizes.n;
+  S.bytes_per_iter = 32.0 * Nv + 48.0 * Nl + 16.0 * n;
+  const double NVp = (double)P.sizes.num_nodes_padded, rows = (double)P.rows.size(), ns = (double)P.sizes.num_slots;
+  S.actual_bytes_per_iter = 2.0 * (4.0 * NVp + 8.0 * rows + 16.0 * ns + 8.0 * Nl) + 2.0 * (8.0 * n + 8.0 * Nl);
+  for (int i = 0; i < 64; ++i) S.hop_histogram[i] = P.hop_histogram[i];
+  *out = ar;
+  return DG_OK;
+}
+
+void dg_destroy(dg_arena* arena) { delete arena; }
+
+dg_status dg_get_stats(const dg_arena* arena, dg_stats* stats) {
+  if (!arena || !stats) return fail(DG_EINVAL, "dg_get_stats: null argument");
+  *stats = arena->stats;
+  return DG_OK;
+}
+
+dg_status dg_init_lambda(dg_arena* ar, void* stream, float* lam, float* M) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M) return fail(DG_EINVAL, "dg_init_lambda: null state");
+  launch_init(ar->dev, lam, M, (cudaStream_t)stream);
+  return check_launch("dg_init_lambda");
+}
+
+dg_status dg_iterate(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
+                     int32_t mode, int32_t iters, double* lb_out, const dg_options* opts) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M) return fail(DG_EINVAL, "dg_iterate: null state");
+  if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_iterate: mode must be 0 or 1");
+  if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_iterate: mode 1 needs omega and alpha");
+  if (iters < 0) return fail(DG_EINVAL, "dg_iterate: negative iteration count");
+  if (opts && opts->block_threads != 0 && (opts->block_threads % 32 != 0 || opts->block_threads > 512))
+    return fail(DG_EINVAL, "dg_iterate: block_threads must be a multiple of 32 in [32, 512]");
+  if (dg_status s = check_vectors("dg_iterate", lam, M, omega, alpha)) return s;
+  return enqueue_iterate(ar, (cudaStream_t)stream, lam, M, omega, alpha, mode, iters, lb_out, opts);
+}
+
+int32_t dg_iterate_launches(const dg_arena* ar, int32_t iters, int32_t want_lb, const dg_options* opts) {
+  (void)ar;
+  (void)opts;
+  int32_t l = 1 + 4 * iters;
+  if (want_lb) l += 2 + (iters == 0 ? 1 : 0);
+  return l;
+}
+
+dg_status dg_sum_M(dg_arena* ar, void* stream, const float* M, float* lam, const float* alpha, int32_t mode,
+                   int32_t renorm) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!M || (renorm && !lam)) return fail(DG_EINVAL, "dg_sum_M: null pointer");
+  if (renorm && mode == 1 && !alpha) return fail(DG_EINVAL, "dg_sum_M: mode 1 needs alpha");
+  launch_reduce_S(ar->dev, M, lam, alpha, mode, renorm != 0, (cudaStream_t)stream);
+  return check_launch("dg_sum_M");
+}
+
+dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
+                   int32_t mode, int32_t forward, int32_t want_energy, const dg_options* opts) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M) return fail(DG_EINVAL, "dg_sweep: null state");
+  if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_sweep: mode must be 0 or 1");
+  if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_sweep: mode 1 needs omega and alpha");
+  if (forward && want_energy) return fail(DG_EINVAL, "dg_sweep: energies come from backward sweeps");
+  if (dg_status s = check_vectors("dg_sweep", lam, M, omega, alpha)) return s;
+  SweepArgs a{};
+  a.lam = lam;
+  a.M = M;
+  a.omega = omega;
+  a.alpha = alpha;
+  a.omega0 = omega_of(opts);
+  a.mode = mode;
+  a.E = want_energy ? ar->dev.E : nullptr;
+  launch_sweep(forward ? kFwd : kBwd, ar->dev, a, threads_of(opts), ar->smem_sweep, (cudaStream_t)stream);
+  return check_launch("dg_sweep");
+}
+
+dg_status dg_bound_from_energies(dg_arena* ar, void* stream, double* lb_out) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lb_out) return fail(DG_EINVAL, "dg_bound_from_energies: null output");
+  launch_lower_bound(ar->dev, lb_out, (cudaStream_t)stream);
+  return check_launch("dg_bound_from_energies");
+}
+
+dg_status dg_min_marginals(dg_arena* ar, void* stream, const float* lam, float* m0, float* m1) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !m0 || !m1) return fail(DG_EINVAL, "dg_min_marginals: null pointer");
+  if (dg_status s = check_vectors("dg_min_marginals", lam, m0, m1)) return s;
+  SweepArgs a{};
+  a.lam = const_cast<float*>(lam);
+  a.M = m0;
+  a.out2 = m1;
+  launch_sweep(kMinMarg, ar->dev, a, 256, ar->smem_sweep, (cudaStream_t)stream);
+  return check_launch("dg_min_marginals");
+}
+
+dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const float* M, double* lb, float* E_per_row) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M || !lb) return fail(DG_EINVAL, "dg_lower_bound: null pointer");
+  if (dg_status s = check_vectors("dg_lower_bound", lam, M)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  SweepArgs a{};
+  a.lam = const_cast<float*>(lam);
+  a.E = ar->dev.E;
+  launch_sweep(kEnergy, ar->dev, a, 256, ar->smem_sweep, st);
+  launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
+  launch_lower_bound(ar->dev, lb, st);
+  if (E_per_row) {
+    cudaError_t e = cudaMemcpyAsync(E_per_row, ar->dev.E, (size_t)ar->dev.m * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "dg_lower_bound copy");
+  }
+  return check_launch("dg_lower_bound");
+}
+
+dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* M, float* g_lam, float* g_M) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M || !g_lam || !g_M) return fail(DG_EINVAL, "dg_lb_seed: null pointer");
+  if (dg_status s = check_vectors("dg_lb_seed", lam, g_lam)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  SweepArgs a{};
+  a.lam = const_cast<float*>(lam);
+  a.M = g_lam;
+  launch_sweep(kSeed, ar->dev, a, 256, ar->smem_sweep, st);
+  launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
+  launch_seed_M(ar->dev, g_M, st);
+  return check_launch("dg_lb_seed");
+}
+
+dg_status dg_graph_create(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
+                          int32_t mode, int32_t iters, double* lb_out, const dg_options* opts, dg_graph_t** out) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!out) return fail(DG_EINVAL, "dg_graph_create: null out");
+  *out = nullptr;
+  if (!lam || !M) return fail(DG_EINVAL, "dg_graph_create: null state");
+  if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_graph_create: mode 1 needs omega and alpha");
+  if (dg_status s = check_vectors("dg_graph_create", lam, M, omega, alpha)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return fail(DG_EINVAL, "dg_graph_create: capture needs a non-default stream");
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_graph_create: begin capture");
+  dg_status s = enqueue_iterate(ar, st, lam, M, omega, alpha, mode, iters, lb_out, opts);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(st, &g);
+  if (s != DG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dg_graph_create: end capture");
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "dg_graph_create: instantiate");
+  }
+  dg_graph_t* G = new dg_graph_t();
+  G->graph = g;
+  G->exec = x;
+  *out = G;
+  return DG_OK;
+}
+
+dg_status dg_graph_replay(dg_graph_t* g, void* stream) {
+  if (!g) return fail(DG_EINVAL, "dg_graph_replay: null graph");
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_graph_replay");
+  return DG_OK;
+}
+
+void dg_graph_destroy(dg_graph_t* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+size_t dg_backward_workspace_bytes(const dg_arena* ar, int32_t iters, int32_t ckpt_every) {
+  (void)ar;
+  (void)iters;
+  (void)ckpt_every;
+  return 0;
+}
+
+dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float* M0, const float* omega,
+                      const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
+                      const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha, void* workspace,
+                      size_t ws_bytes, const dg_options* opts) {
+  (void)ar; (void)stream; (void)lam0; (void)M0; (void)omega; (void)alpha; (void)mode; (void)iters;
+  (void)ckpt_every; (void)g_lam_T; (void)g_M_T; (void)g_lam0; (void)g_M0; (void)g_omega; (void)g_alpha;
+  (void)workspace; (void)ws_bytes; (void)opts;
+  return fail(DG_ESTATE, "dg_backward: not available in this build");
+}
+
+}  // extern "C"

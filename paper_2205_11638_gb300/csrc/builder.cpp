@@ -1,0 +1,499 @@
+// builder.cpp -- host side of dg_plan: rows -> canonical quasi-reduced BDDs
+// -> tiles -> the structure-of-arrays image of the device arena.
+//
+// BDDs (App. B of DOGE-Train): one per constraint row; level h holds the nodes
+// of the row's h-th variable (ascending variable id), every root-to-top path
+// meets one node per level and the paths are exactly the feasible
+// assignments.  A node is identified with the set of feasible completions of
+// the partial sums that reach it; nodes of a level are ordered by
+// (lo rank, hi rank) with bottom = -2 < top = -1 < ranks, so that the
+// minimal quasi-reduced BDD of a row is one fixed table.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+
+constexpr int kCodeBot = -2;
+constexpr int kCodeTop = -1;
+constexpr size_t kMaxStatesPerRow = size_t(1) << 22;
+
+struct RowResult {
+  int status = 0;  // dg_status
+  std::string msg;
+};
+
+// Scratch reused across the rows one host thread builds.
+struct RowScratch {
+  std::vector<int64_t> sums;      // reachable partial sums, level by level
+  std::vector<size_t> lvl;        // level offsets into sums
+  std::vector<int32_t> code;      // code of every (level, sum)
+  std::vector<uint32_t> keys;     // (lo+2) << 16 | (hi+2) per sum of a level
+  std::vector<uint32_t> uniq;
+  std::vector<int64_t> merged;
+};
+
+inline bool row_holds(int64_t act, int sense, int64_t rhs) {
+  switch (sense) {
+    case 0: return act <= rhs;
+    case 1: return act >= rhs;
+    default: return act == rhs;
+  }
+}
+
+// Builds the BDD of one row; appends the level widths to `width` and the
+// child ranks of every node to lo/hi.
+RowResult build_row(const int32_t* a, int k, int sense, int64_t rhs, RowScratch& sc, std::vector<uint8_t>& width,
+                    std::vector<int8_t>& lo, std::vector<int8_t>& hi) {
+  RowResult res;
+  // 1. partial sums reachable from the root, per level (sorted, unique)
+  sc.sums.clear();
+  sc.lvl.assign(1, 0);
+  sc.sums.push_back(0);
+  sc.lvl.push_back(1);
+  for (int h = 0; h < k; ++h) {
+    size_t b = sc.lvl[h], e = sc.lvl[h + 1];
+    sc.merged.clear();
+    size_t p = b, q = b;
+    while (p < e || q < e) {  // merge {s} and {s + a_h}, both ascending
+      int64_t x = p < e ? sc.sums[p] : INT64_MAX;
+      int64_t y = q < e ? sc.sums[q] + a[h] : INT64_MAX;
+      int64_t v = std::min(x, y);
+      if (x == v) ++p;
+      if (y == v) ++q;
+      if (sc.merged.empty() || sc.merged.back() != v) sc.merged.push_back(v);
+    }
+    sc.sums.insert(sc.sums.end(), sc.merged.begin(), sc.merged.end());
+    sc.lvl.push_back(sc.sums.size());
+    if (sc.sums.size() > kMaxStatesPerRow) {
+      res.status = DG_EINVAL;
+      res.msg = "row has too many distinct partial sums for the BDD builder";
+      return res;
+    }
+  }
+  // 2. codes bottom-up
+  sc.code.assign(sc.sums.size(), kCodeBot);
+  for (size_t q = sc.lvl[k]; q < sc.lvl[k + 1]; ++q) sc.code[q] = row_holds(sc.sums[q], sense, rhs) ? kCodeTop : kCodeBot;
+  const size_t width_base = width.size();
+  width.resize(width_base + k);
+  // level nodes are emitted top-down at the end; remember the unique keys
+  std::vector<std::vector<uint32_t>> level_keys(k);
+  for (int h = k - 1; h >= 0; --h) {
+    const size_t b = sc.lvl[h], e = sc.lvl[h + 1];
+    const size_t nb = sc.lvl[h + 1], ne = sc.lvl[h + 2];
+    const int64_t* nxt = sc.sums.data() + nb;
+    const size_t nn = ne - nb;
+    sc.keys.resize(e - b);
+    for (size_t q = b; q < e; ++q) {
+      const int64_t s = sc.sums[q];
+      size_t i0 = std::lower_bound(nxt, nxt + nn, s) - nxt;
+      size_t i1 = std::lower_bound(nxt, nxt + nn, s + a[h]) - nxt;
+      int c0 = sc.code[nb + i0], c1 = sc.code[nb + i1];
+      sc.keys[q - b] = (uint32_t(c0 + 2) << 16) | uint32_t(c1 + 2);
+    }
+    sc.uniq.assign(sc.keys.begin(), sc.keys.end());
+    std::sort(sc.uniq.begin(), sc.uniq.end());
+    sc.uniq.erase(std::unique(sc.uniq.begin(), sc.uniq.end()), sc.uniq.end());
+    if (!sc.uniq.empty() && sc.uniq.front() == 0u) sc.uniq.erase(sc.uniq.begin());  // (bottom, bottom)
+    if (sc.uniq.size() > (size_t)kMaxWidth) {
+      res.status = DG_EINVAL;
+      res.msg = "a BDD level has more than 32 nodes (one level must fit one warp)";
+      return res;
+    }
+    for (size_t q = b; q < e; ++q) {
+      uint32_t key = sc.keys[q - b];
+      sc.code[q] = key == 0u ? kCodeBot
+                             : int(std::lower_bound(sc.uniq.begin(), sc.uniq.end(), key) - sc.uniq.begin());
+    }
+    level_keys[h] = sc.uniq;
+  }
+  if (sc.code[0] == kCodeBot) {
+    res.status = DG_EINFEASIBLE;
+    res.msg = "row has no feasible assignment";
+    return res;
+  }
+  for (int h = 0; h < k; ++h) {
+    bool zero_ok = false, one_ok = false;
+    for (uint32_t key : level_keys[h]) {
+      int c0 = int(key >> 16) - 2, c1 = int(key & 0xFFFFu) - 2;
+      lo.push_back((int8_t)c0);
+      hi.push_back((int8_t)c1);
+      zero_ok |= c0 != kCodeBot;
+      one_ok |= c1 != kCodeBot;
+    }
+    width[width_base + h] = (uint8_t)level_keys[h].size();
+    if (!zero_ok || !one_ok) {
+      res.status = DG_EFORCED;
+      res.msg = "row fixes one of its variables (presolve it away)";
+      return res;
+    }
+  }
+  return res;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
+  if (!R || !R->row_ptr || !R->col || !R->coef || !R->sense || !R->rhs || !R->c)
+    return fail(DG_EINVAL, "dg_plan: null row array");
+  const int32_t n = R->n;
+  const int64_t m = R->m;
+  if (n < 0 || m < 0) return fail(DG_EINVAL, "dg_plan: negative sizes");
+  if (R->row_ptr[0] != 0) return fail(DG_EINVAL, "dg_plan: row_ptr[0] must be 0");
+  const int64_t nnz = R->row_ptr[m];
+  if (nnz > (int64_t)INT32_MAX / 2) return fail(DG_EINVAL, "dg_plan: too many nonzeros");
+  for (int64_t j = 0; j < m; ++j) {
+    const int64_t b = R->row_ptr[j], e = R->row_ptr[j + 1];
+    if (e <= b) return fail(DG_EINVAL, "dg_plan: empty row " + std::to_string(j));
+    if (e - b > 4096) return fail(DG_EINVAL, "dg_plan: row longer than 4096 variables");
+    if (R->sense[j] < 0 || R->sense[j] > 2) return fail(DG_EINVAL, "dg_plan: sense must be 0, 1 or 2");
+    for (int64_t s = b; s < e; ++s) {
+      if (R->col[s] < 0 || R->col[s] >= n || (s > b && R->col[s] <= R->col[s - 1]))
+        return fail(DG_EINVAL, "dg_plan: columns of row " + std::to_string(j) + " must be ascending ids in [0,n)");
+    }
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (!(R->c[i] == R->c[i]) || R->c[i] == 1.0 / 0.0 || R->c[i] == -1.0 / 0.0)
+      return fail(DG_EINVAL, "dg_plan: non-finite cost");
+  // instances
+  int32_t ni = R->num_inst <= 1 || !R->inst_row_ptr || !R->inst_var_ptr ? 1 : R->num_inst;
+  P.inst_row_ptr.resize(ni + 1);
+  P.inst_var_ptr.resize(ni + 1);
+  if (ni == 1) {
+    P.inst_row_ptr = {0, m};
+    P.inst_var_ptr = {0, n};
+  } else {
+    for (int k = 0; k <= ni; ++k) {
+      P.inst_row_ptr[k] = R->inst_row_ptr[k];
+      P.inst_var_ptr[k] = R->inst_var_ptr[k];
+    }
+    if (P.inst_row_ptr[0] != 0 || P.inst_row_ptr[ni] != m || P.inst_var_ptr[0] != 0 || P.inst_var_ptr[ni] != n)
+      return fail(DG_EINVAL, "dg_plan: instance pointers must span all rows and variables");
+    for (int k = 0; k < ni; ++k) {
+      if (P.inst_row_ptr[k + 1] < P.inst_row_ptr[k] || P.inst_var_ptr[k + 1] < P.inst_var_ptr[k])
+        return fail(DG_EINVAL, "dg_plan: instance pointers must be non-decreasing");
+      for (int64_t j = P.inst_row_ptr[k]; j < P.inst_row_ptr[k + 1]; ++j)
+        for (int64_t s = R->row_ptr[j]; s < R->row_ptr[j + 1]; ++s)
+          if (R->col[s] < P.inst_var_ptr[k] || R->col[s] >= P.inst_var_ptr[k + 1])
+            return fail(DG_EINVAL, "dg_plan: row uses a variable of another instance");
+    }
+  }
+
+  // ---- 1. BDDs, in parallel over contiguous row ranges --------------------
+  int nthreads = opts && opts->num_threads > 0 ? opts->num_threads : (int)std::thread::hardware_concurrency();
+  nthreads = std::max(1, std::min<int>(nthreads, (int)std::max<int64_t>(1, m / 4096)));
+  struct Part {
+    std::vector<uint8_t> width;
+    std::vector<int8_t> lo, hi;
+    std::vector<int32_t> nodes_of_row;
+    RowResult err;
+    int64_t err_row = -1;
+  };
+  std::vector<Part> parts(nthreads);
+  std::vector<int64_t> cut(nthreads + 1);
+  for (int t = 0; t <= nthreads; ++t) cut[t] = m * t / nthreads;
+  auto worker = [&](int t) {
+    RowScratch sc;
+    Part& pt = parts[t];
+    pt.nodes_of_row.reserve(cut[t + 1] - cut[t]);
+    for (int64_t j = cut[t]; j < cut[t + 1]; ++j) {
+      const int64_t b = R->row_ptr[j];
+      const int k = (int)(R->row_ptr[j + 1] - b);
+      size_t before = pt.lo.size();
+      RowResult r = build_row(R->coef + b, k, R->sense[j], R->rhs[j], sc, pt.width, pt.lo, pt.hi);
+      if (r.status != 0) {
+        pt.err = r;
+        pt.err_row = j;
+        return;
+      }
+      pt.nodes_of_row.push_back((int32_t)(pt.lo.size() - before));
+    }
+  };
+  if (nthreads == 1) {
+    worker(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nthreads; ++t) th.emplace_back(worker, t);
+    for (auto& x : th) x.join();
+  }
+  for (int t = 0; t < nthreads; ++t)
+    if (parts[t].err.status != 0)
+      return fail((dg_status)parts[t].err.status, "dg_plan: row " + std::to_string(parts[t].err_row) + ": " +
+                                                      parts[t].err.msg);
+  std::vector<uint8_t> width;
+  width.reserve(nnz);
+  P.node_ptr.assign(m + 1, 0);
+  {
+    int64_t j = 0;
+    for (int t = 0; t < nthreads; ++t) {
+      width.insert(width.end(), parts[t].width.begin(), parts[t].width.end());
+      P.lo8.insert(P.lo8.end(), parts[t].lo.begin(), parts[t].lo.end());
+      P.hi8.insert(P.hi8.end(), parts[t].hi.begin(), parts[t].hi.end());
+      for (int32_t c : parts[t].nodes_of_row) {
+        P.node_ptr[j + 1] = P.node_ptr[j] + c;
+        ++j;
+      }
+      std::vector<uint8_t>().swap(parts[t].width);
+      std::vector<int8_t>().swap(parts[t].lo);
+      std::vector<int8_t>().swap(parts[t].hi);
+    }
+  }
+  P.row_ptr.assign(R->row_ptr, R->row_ptr + m + 1);
+  const int64_t num_nodes = P.node_ptr[m];
+
+  // ---- 2. tiles: BDDs sorted longest first, packed greedily ---------------
+  const int tile_nodes = opts && opts->tile_nodes > 0 ? (opts->tile_nodes + 31) / 32 * 32 : 2048;
+  const int tile_slots = opts && opts->tile_slots > 0 ? opts->tile_slots : 1024;
+  const int tile_rows_budget = std::max(1, tile_nodes / kWarp);
+  std::vector<int64_t> order(m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+    int64_t kx = R->row_ptr[x + 1] - R->row_ptr[x], ky = R->row_ptr[y + 1] - R->row_ptr[y];
+    if (kx != ky) return kx > ky;
+    return (P.node_ptr[x + 1] - P.node_ptr[x]) > (P.node_ptr[y + 1] - P.node_ptr[y]);
+  });
+  int max_hops = 0, max_width = 0;
+  for (int64_t j = 0; j < m; ++j) {
+    int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
+    max_hops = std::max(max_hops, k);
+    P.hop_histogram[std::min(k, 63)]++;
+  }
+  for (uint8_t w : width) max_width = std::max<int>(max_width, w);
+
+  // pass A: decide tile membership
+  struct TileBuild {
+    int64_t first, last;  // range in `order`
+  };
+  std::vector<TileBuild> tb;
+  {
+    std::vector<int> rows_h, used_h;
+    int64_t start = 0;
+    int nh = 0, total_rows = 0, total_slots = 0;
+    auto reset = [&](int64_t s, int hops) {
+      start = s;
+      nh = hops;
+      rows_h.assign(hops, 0);
+      used_h.assign(hops, 0);
+      total_rows = total_slots = 0;
+    };
+    for (int64_t q = 0; q < m; ++q) {
+      const int64_t j = order[q];
+      const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
+      if (q == 0) reset(0, k);
+      // tentative add
+      int add_rows = 0;
+      for (int h = 0; h < k; ++h) {
+        int w = width[R->row_ptr[j] + h];
+        if (rows_h[h] == 0 || used_h[h] + w > kWarp) add_rows++;
+      }
+      bool fits = total_rows + add_rows <= tile_rows_budget && total_slots + k <= tile_slots;
+      if (!fits && q > start) {
+        tb.push_back({start, q});
+        reset(q, k);
+        add_rows = k;  // every level opens a row in an empty tile
+      }
+      for (int h = 0; h < k; ++h) {
+        int w = width[R->row_ptr[j] + h];
+        if (rows_h[h] == 0 || used_h[h] + w > kWarp) {
+          rows_h[h]++;
+          used_h[h] = w;
+        } else {
+          used_h[h] += w;
+        }
+      }
+      total_rows += add_rows;
+      total_slots += k;
+      (void)nh;
+    }
+    if (m > 0) tb.push_back({start, m});
+  }
+
+  // pass B: lay out every tile
+  const int T = (int)tb.size();
+  P.tiles.resize(T);
+  P.slot_to_csr.clear();
+  std::vector<int64_t> slot_of_csr(nnz, -1);
+  int64_t row_base = 0, slot_base = 0, hop_base = 0;
+  size_t smem_max = 0, smem_adj_max = 0;
+  for (int t = 0; t < T; ++t) {
+    const int64_t q0 = tb[t].first, q1 = tb[t].last;
+    const int nh = (int)(R->row_ptr[order[q0] + 1] - R->row_ptr[order[q0]]);
+    // per hop: layers in BDD order -> rows
+    std::vector<std::vector<int>> layer_row(q1 - q0), layer_lane(q1 - q0);
+    std::vector<int> rows_h(nh, 0), used_h(nh, 0);
+    std::vector<int> nslots_h(nh, 0);
+    int maxw = 1;
+    for (int64_t q = q0; q < q1; ++q) {
+      const int64_t j = order[q];
+      const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
+      layer_row[q - q0].resize(k);
+      layer_lane[q - q0].resize(k);
+      for (int h = 0; h < k; ++h) {
+        int w = width[R->row_ptr[j] + h];
+        maxw = std::max(maxw, w);
+        if (rows_h[h] == 0 || used_h[h] + w > kWarp) {
+          rows_h[h]++;
+          used_h[h] = 0;
+        }
+        layer_row[q - q0][h] = rows_h[h] - 1;
+        layer_lane[q - q0][h] = used_h[h];
+        used_h[h] += w;
+        nslots_h[h]++;
+      }
+    }
+    std::vector<int> row_off(nh + 1, 0), slot_off(nh + 1, 0);
+    for (int h = 0; h < nh; ++h) {
+      row_off[h + 1] = row_off[h] + rows_h[h];
+      slot_off[h + 1] = slot_off[h] + nslots_h[h];
+    }
+    const int nrows = row_off[nh];
+    const int nslots_real = slot_off[nh];
+    const int nslots = (nslots_real + 3) / 4 * 4;
+    if (nrows > 65535 || nslots > 65535) return fail(DG_EINVAL, "dg_plan: a tile exceeds 65535 rows or slots");
+    Tile& tile = P.tiles[t];
+    tile.row_base = (int32_t)row_base;
+    tile.slot_base = (int32_t)slot_base;
+    tile.hop_base = (int32_t)hop_base;
+    tile.nrows = nrows;
+    tile.nslots = nslots;
+    tile.nhops = nh;
+    tile.maxw = maxw;
+    tile.nbdd = (int32_t)(q1 - q0);
+    for (int h = 0; h <= nh; ++h) P.hoptab.push_back((uint32_t)row_off[h] | ((uint32_t)slot_off[h] << 16));
+    // rows and nodes
+    const size_t rbase = P.rows.size();
+    P.rows.resize(rbase + nrows, RowMeta{0u, 0u});
+    P.lohi.resize((rbase + nrows) * kWarp, 0xFFFFFFFFu);
+    P.slot_var.resize(slot_base + nslots, -1);
+    P.slot_row.resize(slot_base + nslots, -1);
+    P.slot_to_csr.resize(slot_base + nslots, -1);
+    std::vector<int> slot_cursor(nh, 0);
+    for (int64_t q = q0; q < q1; ++q) {
+      const int64_t j = order[q];
+      const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
+      const int64_t nb = P.node_ptr[j];
+      int64_t nodes_seen = 0;
+      for (int h = 0; h < k; ++h) {
+        const int64_t csr = R->row_ptr[j] + h;
+        const int w = width[csr];
+        const int r_local = row_off[h] + layer_row[q - q0][h];
+        const int lane0 = layer_lane[q - q0][h];
+        const int s_local = slot_off[h] + slot_cursor[h]++;
+        RowMeta& rm = P.rows[rbase + r_local];
+        if (rm.head == 0u) rm.info = (uint32_t)s_local;  // first layer of the row
+        rm.head |= 1u << lane0;
+        rm.info = (rm.info & 0xFFFFu) | ((uint32_t)(lane0 + w) << 16);
+        const int64_t as = slot_base + s_local;
+        P.slot_var[as] = R->col[csr];
+        P.slot_row[as] = (int32_t)j;
+        P.slot_to_csr[as] = csr;
+        slot_of_csr[csr] = as;
+        for (int r = 0; r < w; ++r) {
+          const int8_t c0 = P.lo8[nb + nodes_seen + r], c1 = P.hi8[nb + nodes_seen + r];
+          auto child = [&](int8_t cc) -> uint32_t {
+            if (cc == kCodeBot) return kBot;
+            if (cc == kCodeTop) return kTop;
+            const int rr = row_off[h + 1] + layer_row[q - q0][h + 1];
+            return (uint32_t)(rr * kWarp + layer_lane[q - q0][h + 1] + cc);
+          };
+          P.lohi[(rbase + r_local) * kWarp + lane0 + r] = child(c0) | (child(c1) << 16);
+        }
+        nodes_seen += w;
+      }
+    }
+    smem_max = std::max(smem_max, sweep_smem_bytes(nrows, nslots, nh));
+    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nrows, nslots, nh));
+    P.max_tile_rows = std::max(P.max_tile_rows, nrows);
+    P.max_tile_slots = std::max(P.max_tile_slots, nslots);
+    P.max_tile_hops = std::max(P.max_tile_hops, nh);
+    row_base += nrows;
+    slot_base += nslots;
+    hop_base += nh + 1;
+  }
+  const int64_t num_slots = slot_base;
+  if (num_slots >= (int64_t)INT32_MAX || row_base * kWarp >= (int64_t)INT32_MAX)
+    return fail(DG_EINVAL, "dg_plan: arena exceeds 2^31 slots or nodes");
+
+  // ---- 3. variable CSR (slots of each variable, rows ascending) -----------
+  P.var_ptr.assign(n + 1, 0);
+  for (int64_t s = 0; s < nnz; ++s) P.var_ptr[R->col[s] + 1]++;
+  for (int32_t i = 0; i < n; ++i) P.var_ptr[i + 1] += P.var_ptr[i];
+  P.var_slots.assign(nnz, 0);
+  {
+    std::vector<int32_t> cur(P.var_ptr.begin(), P.var_ptr.end() - 1);
+    for (int64_t s = 0; s < nnz; ++s) P.var_slots[cur[R->col[s]]++] = (int32_t)slot_of_csr[s];
+  }
+  P.c.assign(R->c, R->c + n);
+  P.invdeg.assign(n, 0.0f);
+  for (int32_t i = 0; i < n; ++i) {
+    int d = P.var_ptr[i + 1] - P.var_ptr[i];
+    P.invdeg[i] = d > 0 ? (float)(1.0 / d) : 0.0f;
+  }
+  // ---- 4. lower-bound chunks: per instance its rows, then its variables ----
+  const int kChunk = 4096;
+  P.inst_chunk_ptr.assign(ni + 1, 0);
+  for (int k = 0; k < ni; ++k) {
+    for (int kind = 0; kind < 2; ++kind) {
+      int64_t b = kind == 0 ? P.inst_row_ptr[k] : P.inst_var_ptr[k];
+      int64_t e = kind == 0 ? P.inst_row_ptr[k + 1] : P.inst_var_ptr[k + 1];
+      for (int64_t x = b; x < e; x += kChunk) {
+        P.lb_chunks.insert(P.lb_chunks.end(), {k, kind, (int32_t)x, (int32_t)std::min<int64_t>(e, x + kChunk)});
+      }
+    }
+    P.inst_chunk_ptr[k + 1] = (int32_t)(P.lb_chunks.size() / 4);
+  }
+  const int num_chunks = (int)(P.lb_chunks.size() / 4);
+
+  // ---- 5. arena offsets ----------------------------------------------------
+  size_t o = 0;
+  auto put = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1), 256);
+    return at;
+  };
+  P.off.tiles = put(P.tiles.size() * sizeof(Tile));
+  P.off.hoptab = put(P.hoptab.size() * 4);
+  P.off.rows = put(P.rows.size() * sizeof(RowMeta));
+  P.off.lohi = put(P.lohi.size() * 4);
+  P.off.slot_var = put(num_slots * 4);
+  P.off.slot_row = put(num_slots * 4);
+  P.off.var_ptr = put((size_t)(n + 1) * 4);
+  P.off.var_slots = put((size_t)nnz * 4);
+  P.off.c = put((size_t)n * 8);
+  P.off.invdeg = put((size_t)n * 4);
+  P.off.inst_row_ptr = put((size_t)(ni + 1) * 8);
+  P.off.inst_var_ptr = put((size_t)(ni + 1) * 4);
+  P.off.lb_chunks = put((size_t)num_chunks * 16);
+  P.off.inst_chunk_ptr = put((size_t)(ni + 1) * 4);
+  P.off.S = put((size_t)n * 4);
+  P.off.E = put((size_t)m * 4);
+  P.off.lb_part = put((size_t)num_chunks * 8);
+  P.off.total = o;
+  P.smem_sweep = align_up(smem_max, 16);
+  P.smem_adjoint = align_up(smem_adj_max, 16);
+
+  dg_sizes& z = P.sizes;
+  z.arena_bytes = P.off.total;
+  z.num_slots = num_slots;
+  z.num_lambda = nnz;
+  z.num_nodes = num_nodes;
+  z.num_nodes_padded = row_base * kWarp;
+  z.n = n;
+  z.m = m;
+  z.num_inst = ni;
+  z.num_tiles = T;
+  z.max_hops = max_hops;
+  z.max_width = max_width;
+  z.smem_bytes = P.smem_sweep;
+  return DG_OK;
+}
+
+}  // namespace dg

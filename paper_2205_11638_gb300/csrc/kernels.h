@@ -1,0 +1,35 @@
+// kernels.h -- host-side launchers of the libdg kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+enum SweepKind : int { kFwd = 0, kBwd = 1, kMinMarg = 2, kEnergy = 3, kSeed = 4 };
+
+struct SweepArgs {
+  float* lam;          // in/out (read-only for kMinMarg/kEnergy/kSeed)
+  float* M;            // out: M (kFwd/kBwd), m0 (kMinMarg), g_lam (kSeed)
+  float* out2;         // out: m1 (kMinMarg)
+  const float* omega;  // mode 1
+  const float* alpha;  // mode 1
+  float omega0;        // mode 0
+  int mode;
+  float* E;            // nullable: E^j per original row (kBwd, kEnergy)
+};
+
+cudaError_t set_sweep_smem_limit(size_t bytes);
+void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, size_t smem, cudaStream_t st);
+
+// S_i = sum_{k in J_i} M_ik in fixed slot order; with renorm, also
+// lambda_ij += alpha_ij * (c_i - sum_k (lambda_ik + M_ik)) computed in FP64.
+void launch_reduce_S(const DevArena& A, const float* M, float* lam, const float* alpha, int mode, bool renorm,
+                     cudaStream_t st);
+void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st);
+// per-instance FP64 lower bound from A.E and A.S
+void launch_lower_bound(const DevArena& A, double* lb_out, cudaStream_t st);
+void launch_seed_M(const DevArena& A, float* g_M, cudaStream_t st);
+
+}  // namespace dg

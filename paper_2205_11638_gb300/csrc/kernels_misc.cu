@@ -1,0 +1,121 @@
+// kernels_misc.cu -- per-variable and per-instance kernels around the sweeps:
+// the deferred min-marginal sums S_i (Alg. 1, lambda update), the FP64
+// re-projection onto the dual constraint of (D), the initial split of c and
+// the FP64 lower bound (Def. 2 with the unary term of the deferred
+// min-marginals).
+#include "kernels.h"
+
+namespace dg {
+
+// S_i = sum_{j in J_i} M_ij over the variable's slots in fixed order.  With
+// renorm the same pass re-projects lambda onto sum_j (lambda_ij + M_ij) = c_i
+// (the invariant of the proof of Prop. 1): the FP64 residual
+// r_i = c_i - sum_j (lambda_ij + M_ij) is spread with the averaging weights.
+template <bool RENORM>
+__global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __restrict__ M, float* lam,
+                                                   const float* __restrict__ alpha, int mode) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
+  float s = 0.f;
+  double tot = 0.0;
+  for (int k = b; k < e; ++k) {
+    const int q = __ldg(A.var_slots + k);
+    const float mk = M[q];
+    s += mk;
+    if (RENORM) tot += (double)lam[q] + (double)mk;
+  }
+  A.S[i] = s;
+  if (RENORM && e > b) {
+    const double r = A.c[i] - tot;
+    const float inv = __ldg(A.invdeg + i);
+    for (int k = b; k < e; ++k) {
+      const int q = __ldg(A.var_slots + k);
+      const double w = mode == 1 ? (double)alpha[q] : (double)inv;
+      lam[q] = (float)((double)lam[q] + w * r);
+    }
+  }
+}
+
+__global__ void k_init(DevArena A, float* lam, float* M) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.num_slots) return;
+  const int var = __ldg(A.slot_var + q);
+  float l = 0.f;
+  if (var >= 0) {
+    const int deg = __ldg(A.var_ptr + var + 1) - __ldg(A.var_ptr + var);
+    l = (float)(A.c[var] / (double)deg);
+  }
+  lam[q] = l;
+  M[q] = 0.f;
+}
+
+// One FP64 partial sum per chunk: rows contribute E^j, variables
+// min(0, S_i) (or min(0, c_i) when no row covers them).
+__global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
+  const int4 ch = __ldg(A.lb_chunks + blockIdx.x);
+  double acc = 0.0;
+  for (int x = ch.z + threadIdx.x; x < ch.w; x += blockDim.x) {
+    if (ch.y == 0) {
+      acc += (double)A.E[x];
+    } else {
+      const int deg = __ldg(A.var_ptr + x + 1) - __ldg(A.var_ptr + x);
+      acc += deg > 0 ? fmin(0.0, (double)A.S[x]) : fmin(0.0, A.c[x]);
+    }
+  }
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    A.lb_part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_lb_final(DevArena A, double* lb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= A.num_inst) return;
+  double t = 0.0;
+  for (int c = A.inst_chunk_ptr[k]; c < A.inst_chunk_ptr[k + 1]; ++c) t += A.lb_part[c];
+  lb[k] = t;
+}
+
+__global__ void k_seed_M(DevArena A, float* gM) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.num_slots) return;
+  const int var = __ldg(A.slot_var + q);
+  gM[q] = (var >= 0 && A.S[var] < 0.f) ? 1.f : 0.f;
+}
+
+void launch_reduce_S(const DevArena& A, const float* M, float* lam, const float* alpha, int mode, bool renorm,
+                     cudaStream_t st) {
+  const int T = 256;
+  const int G = (A.n + T - 1) / T;
+  if (G == 0) return;
+  if (renorm)
+    k_reduce_S<true><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
+  else
+    k_reduce_S<false><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
+}
+
+void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st) {
+  const int T = 256;
+  const int64_t G = (A.num_slots + T - 1) / T;
+  if (G > 0) k_init<<<(unsigned)G, T, 0, st>>>(A, lam, M);
+}
+
+void launch_lower_bound(const DevArena& A, double* lb, cudaStream_t st) {
+  if (A.num_lb_chunks > 0) k_lb_partial<<<A.num_lb_chunks, 256, 0, st>>>(A);
+  k_lb_final<<<(A.num_inst + 127) / 128, 128, 0, st>>>(A, lb);
+}
+
+void launch_seed_M(const DevArena& A, float* gM, cudaStream_t st) {
+  const int T = 256;
+  const int64_t G = (A.num_slots + T - 1) / T;
+  if (G > 0) k_seed_M<<<(unsigned)G, T, 0, st>>>(A, gM);
+}
+
+}  // namespace dg

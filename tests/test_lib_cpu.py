@@ -1,0 +1,130 @@
+"""CPU-side checks of libdg: the library loads and exports every function of
+include/dg.h, and the host builder (dg_plan) produces the canonical BDDs the
+oracle builds independently, bit for bit, with the documented status codes.
+No kernel is launched here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_2205_11638_gb300 import _lib, build, solver
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "dg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    lib = _lib.load()
+    names = _declared_functions()
+    assert len(names) >= 20
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(names) == set(_lib.SIGNATURES)
+
+
+def test_struct_layouts(tmp_path):
+    """The ctypes mirrors have the C layout of include/dg.h (sizes and offsets
+    printed by a C program compiled against the header)."""
+    src = tmp_path / "layout.c"
+    src.write_text(
+        "#include <stdio.h>\n#include <stddef.h>\n#include \"dg.h\"\n"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(dg_rows), sizeof(dg_options),"
+        " sizeof(dg_sizes), sizeof(dg_stats), offsetof(dg_rows, m), offsetof(dg_sizes, m),"
+        " offsetof(dg_stats, hop_histogram)); return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(_lib.dg_rows), ctypes.sizeof(_lib.dg_options), ctypes.sizeof(_lib.dg_sizes),
+            ctypes.sizeof(_lib.dg_stats), _lib.dg_rows.m.offset, _lib.dg_sizes.m.offset,
+            _lib.dg_stats.hop_histogram.offset]
+    assert got == want
+
+
+@pytest.mark.parametrize("make", [lambda: workloads.set_cover(), lambda: workloads.independent_set(n=1500, seed=4),
+                                  lambda: workloads.matching_quadratic(L=30, R=30, pairs=900, seed=5),
+                                  lambda: workloads.tracking(frames=4, dets=40, seed=6),
+                                  lambda: workloads.batched_mix(num=6, scale=0.01)[0]])
+def test_plan_structure_bit_exact_vs_oracle(make):
+    prob = make()
+    P = solver.plan(prob)
+    O = oracle.Oracle(prob)
+    assert P.sizes.num_nodes == O.num_nodes
+    assert P.sizes.num_lambda == O.num_slots
+    for j in range(P.m):
+        for a, b in zip(P.bdd(j), O.bdd(j)):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_plan_random_rows_bit_exact():
+    rows = []
+    for r in workloads.random_rows(400, kmax=12, n=40, seed=77):
+        try:
+            oracle.Oracle(workloads.single_rows_problem([r], 40, np.zeros(40)))
+        except oracle.OracleError:
+            continue
+        rows.append(r)
+    prob = workloads.single_rows_problem(rows, 40, np.random.default_rng(0).normal(size=40))
+    P = solver.plan(prob)
+    O = oracle.Oracle(prob)
+    for j in range(P.m):
+        for a, b in zip(P.bdd(j), O.bdd(j)):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_slot_map_is_permutation():
+    prob = workloads.matching_quadratic(L=30, R=30, pairs=900, seed=5)
+    P = solver.plan(prob, tile_nodes=256, tile_slots=128)
+    sm = P.slot_to_csr
+    real = sm[sm >= 0]
+    assert sorted(real.tolist()) == list(range(len(prob["col"])))
+    assert P.sizes.num_tiles > 10
+    assert P.num_slots % 4 == 0
+
+
+def _status_of(rows, n):
+    try:
+        solver.plan(workloads.single_rows_problem(rows, n, np.zeros(n)))
+    except _lib.DgError as e:
+        return e.status
+    return 0
+
+
+def test_status_codes():
+    assert _status_of([(np.array([0, 1]), np.array([2, 2]), 2, 1)], 2) == _lib.DG_EINFEASIBLE
+    assert _status_of([(np.array([0, 1]), np.array([1, 1]), 1, 2)], 2) == _lib.DG_EFORCED
+    # a knapsack row whose BDD has a level of 112 nodes (wider than one warp)
+    a = np.array([28, 31, 45, 57, 3, 9, 49, 56, 15, 19, 52, 25, 17, 49, 16, 25])
+    assert _status_of([(np.arange(16), a, 0, 248)], 16) == _lib.DG_EINVAL
+    bad = workloads.single_rows_problem([(np.array([0, 1]), np.array([1, 1]), 0, 1)], 2, np.zeros(2))
+    bad["col"] = bad["col"][::-1].copy()
+    with pytest.raises(_lib.DgError) as e:
+        solver.plan(bad)
+    assert e.value.status == _lib.DG_EINVAL
+    empty = dict(n=2, row_ptr=np.array([0, 0]), col=np.zeros(0, np.int32), coef=np.zeros(0, np.int32),
+                 sense=np.zeros(1, np.int8), rhs=np.zeros(1, np.int32), c=np.zeros(2))
+    with pytest.raises(_lib.DgError) as e:
+        solver.plan(empty)
+    assert e.value.status == _lib.DG_EINVAL
+
+
+def test_tile_budgets_respected():
+    prob = workloads.tracking(frames=6, dets=60, seed=2)
+    for tn, ts in [(256, 128), (1024, 512), (4096, 2048)]:
+        P = solver.plan(prob, tile_nodes=tn, tile_slots=ts)
+        assert P.sizes.smem_bytes <= 227 * 1024
+        assert P.sizes.num_nodes_padded >= P.sizes.num_nodes
