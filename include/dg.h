@@ -74,9 +74,10 @@ typedef struct dg_rows {
 
 /* Options (zero-initialise, then set what you need; 0 selects the default). */
 typedef struct dg_options {
-  int32_t tile_nodes;    /* node budget of one tile, multiple of 32 (default 2048) */
-  int32_t tile_slots;    /* slot budget of one tile (default 1024) */
-  int32_t block_threads; /* threads per CTA of the sweep kernels (default 256) */
+  int32_t tile_nodes;    /* reserved (tiles hold 32 BDDs, one per lane) */
+  int32_t tile_slots;    /* reserved */
+  int32_t block_threads; /* threads per CTA of the sweep kernels: 32, 64, 96 or
+                            128 (one tile per warp; default 128) */
   int32_t renorm_every;  /* FP64 re-projection of lambda onto sum_j(lambda+M)=c
                             every k iterations (0 = never) */
   float omega;           /* damping of mode 0 (default 0.5 when 0) */
@@ -96,7 +97,9 @@ typedef struct dg_sizes {
   int32_t num_tiles;
   int32_t max_hops;      /* u = longest BDD */
   int32_t max_width;     /* widest BDD level */
-  size_t smem_bytes;     /* dynamic shared memory of the largest tile */
+  size_t smem_bytes;     /* shared memory of the largest tile (one warp) */
+  int32_t num_launch_groups; /* kernel launches per sweep (tiles grouped by
+                                shared-memory footprint) */
 } dg_sizes;
 
 typedef struct dg_stats {

@@ -27,6 +27,7 @@ using namespace dg;
 
 struct dg_arena_s {
   DevArena dev{};
+  std::vector<LaunchGroup> groups;
   dg_sizes sizes{};
   dg_stats stats{};
   size_t smem_sweep = 0, smem_adjoint = 0;
@@ -42,7 +43,7 @@ struct dg_graph_s {
 namespace {
 
 int threads_of(const dg_options* o) {
-  int t = o && o->block_threads > 0 ? o->block_threads : 256;
+  int t = o && o->block_threads > 0 ? o->block_threads : 128;
   t = (t + 31) / 32 * 32;
   return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
@@ -72,10 +73,10 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   launch_reduce_S(A, M, lam, alpha, mode, false, st);
   for (int it = 0; it < iters; ++it) {
     a.E = nullptr;
-    launch_sweep(kFwd, A, a, threads, ar->smem_sweep, st);
+    launch_sweep(kFwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), st);
     launch_reduce_S(A, M, lam, alpha, mode, false, st);
     if (lb_out && it == iters - 1) a.E = A.E;
-    launch_sweep(kBwd, A, a, threads, ar->smem_sweep, st);
+    launch_sweep(kBwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), st);
     const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
     launch_reduce_S(A, M, lam, alpha, mode, rn, st);
   }
@@ -84,7 +85,7 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
       SweepArgs e{};
       e.lam = lam;
       e.E = A.E;
-      launch_sweep(kEnergy, A, e, threads, ar->smem_sweep, st);
+      launch_sweep(kEnergy, A, e, threads, ar->groups.data(), (int)ar->groups.size(), st);
     }
     launch_lower_bound(A, lb_out, st);
   }
@@ -130,7 +131,7 @@ dg_status dg_plan(const dg_rows* rows, const dg_options* opts, dg_plan_t** out, 
     delete p;
     return fail(DG_EINVAL, std::string("dg_plan: ") + e.what());
   }
-  if (p->p.smem_sweep > 227 * 1024 || p->p.smem_adjoint > 227 * 1024) {
+  if (p->p.smem_sweep > 227 * 1024) {
     // a single BDD larger than one CTA's shared memory
     delete p;
     return fail(DG_EINVAL, "dg_plan: a BDD does not fit one tile's shared memory");
@@ -202,9 +203,8 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
     if (bytes) std::memcpy(h.data() + off, src, bytes);
   };
   cp(P.off.tiles, P.tiles.data(), P.tiles.size() * sizeof(Tile));
-  cp(P.off.hoptab, P.hoptab.data(), P.hoptab.size() * 4);
-  cp(P.off.rows, P.rows.data(), P.rows.size() * sizeof(RowMeta));
-  cp(P.off.lohi, P.lohi.data(), P.lohi.size() * 4);
+  cp(P.off.desc, P.desc.data(), P.desc.size() * 2);
+  cp(P.off.lohi8, P.lohi8.data(), P.lohi8.size() * 2);
   cp(P.off.slot_var, P.slot_var.data(), P.slot_var.size() * 4);
   cp(P.off.slot_row, P.slot_row.data(), P.slot_row.size() * 4);
   cp(P.off.var_ptr, P.var_ptr.data(), P.var_ptr.size() * 4);
@@ -226,6 +226,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
     if (e != cudaSuccess) return cuda_fail(e, "dg_bind: device attribute");
     if ((size_t)optin < P.smem_sweep) return fail(DG_EINVAL, "dg_bind: tiles need more shared memory than a CTA has");
     e = set_sweep_smem_limit((size_t)optin);  // same limit for every arena of the process
+    set_cta_smem_cap((size_t)optin);
     if (e != cudaSuccess) return cuda_fail(e, "dg_bind: shared-memory limit");
   }
   dg_arena* ar = new dg_arena();
@@ -233,9 +234,8 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   char* b = (char*)arena_dev;
   DevArena& A = ar->dev;
   A.tiles = (const Tile*)(b + P.off.tiles);
-  A.hoptab = (const uint32_t*)(b + P.off.hoptab);
-  A.rows = (const RowMeta*)(b + P.off.rows);
-  A.lohi = (const uint32_t*)(b + P.off.lohi);
+  A.desc = (const uint16_t*)(b + P.off.desc);
+  A.lohi8 = (const uint16_t*)(b + P.off.lohi8);
   A.slot_var = (const int32_t*)(b + P.off.slot_var);
   A.slot_row = (const int32_t*)(b + P.off.slot_row);
   A.var_ptr = (const int32_t*)(b + P.off.var_ptr);
@@ -247,6 +247,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.lb_chunks = (const int4*)(b + P.off.lb_chunks);
   A.inst_chunk_ptr = (const int32_t*)(b + P.off.inst_chunk_ptr);
   A.S = (float*)(b + P.off.S);
+  A.Sbar = (float*)(b + P.off.Sbar);
   A.E = (float*)(b + P.off.E);
   A.lb_part = (double*)(b + P.off.lb_part);
   A.n = P.sizes.n;
@@ -257,6 +258,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.num_lb_chunks = (int32_t)(P.lb_chunks.size() / 4);
   ar->sizes = P.sizes;
   ar->smem_sweep = P.smem_sweep;
+  ar->groups = P.groups;
   ar->smem_adjoint = P.smem_adjoint;
   ar->max_tile_rows = P.max_tile_rows;
   ar->max_tile_slots = P.max_tile_slots;
@@ -266,8 +268,12 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   S.num_arcs = 2 * P.sizes.num_nodes;
   const double Nv = (double)P.sizes.num_nodes, Nl = (double)P.sizes.num_lambda, n = (double)P.sizes.n;
   S.bytes_per_iter = 32.0 * Nv + 48.0 * Nl + 16.0 * n;
-  const double NVp = (double)P.sizes.num_nodes_padded, rows = (double)P.rows.size(), ns = (double)P.sizes.num_slots;
-  S.actual_bytes_per_iter = 2.0 * (4.0 * NVp + 8.0 * rows + 16.0 * ns + 8.0 * Nl) + 2.0 * (8.0 * n + 8.0 * Nl);
+  const double NVp = (double)P.sizes.num_nodes_padded, ns = (double)P.sizes.num_slots;
+  // per sweep: children 2 B per node; descriptor, variable, lambda read and
+  // write, M write 20 B per slot; alpha and S gathers 8 B per lambda.  Per
+  // S reduction: variable CSR and M gather 8 B per lambda, pointers and S 8 B
+  // per variable.
+  S.actual_bytes_per_iter = 2.0 * (2.0 * NVp + 20.0 * ns + 8.0 * Nl) + 2.0 * (8.0 * n + 8.0 * Nl);
   for (int i = 0; i < 64; ++i) S.hop_histogram[i] = P.hop_histogram[i];
   *out = ar;
   return DG_OK;
@@ -334,7 +340,7 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
   a.omega0 = omega_of(opts);
   a.mode = mode;
   a.E = want_energy ? ar->dev.E : nullptr;
-  launch_sweep(forward ? kFwd : kBwd, ar->dev, a, threads_of(opts), ar->smem_sweep, (cudaStream_t)stream);
+  launch_sweep(forward ? kFwd : kBwd, ar->dev, a, threads_of(opts), ar->groups.data(), (int)ar->groups.size(), (cudaStream_t)stream);
   return check_launch("dg_sweep");
 }
 
@@ -353,7 +359,7 @@ dg_status dg_min_marginals(dg_arena* ar, void* stream, const float* lam, float* 
   a.lam = const_cast<float*>(lam);
   a.M = m0;
   a.out2 = m1;
-  launch_sweep(kMinMarg, ar->dev, a, 256, ar->smem_sweep, (cudaStream_t)stream);
+  launch_sweep(kMinMarg, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(), (cudaStream_t)stream);
   return check_launch("dg_min_marginals");
 }
 
@@ -365,7 +371,7 @@ dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const flo
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
   a.E = ar->dev.E;
-  launch_sweep(kEnergy, ar->dev, a, 256, ar->smem_sweep, st);
+  launch_sweep(kEnergy, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(), st);
   launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
   launch_lower_bound(ar->dev, lb, st);
   if (E_per_row) {
@@ -383,7 +389,7 @@ dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* 
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
   a.M = g_lam;
-  launch_sweep(kSeed, ar->dev, a, 256, ar->smem_sweep, st);
+  launch_sweep(kSeed, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(), st);
   launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
   launch_seed_M(ar->dev, g_M, st);
   return check_launch("dg_lb_seed");

@@ -249,13 +249,21 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.row_ptr.assign(R->row_ptr, R->row_ptr + m + 1);
   const int64_t num_nodes = P.node_ptr[m];
 
-  // ---- 2. tiles: BDDs sorted longest first, packed greedily ---------------
-  const int tile_nodes = opts && opts->tile_nodes > 0 ? (opts->tile_nodes + 31) / 32 * 32 : 2048;
-  const int tile_slots = opts && opts->tile_slots > 0 ? opts->tile_slots : 1024;
-  const int tile_rows_budget = std::max(1, tile_nodes / kWarp);
+  // ---- 2. tiles: 32 BDDs per tile, one per lane ---------------------------
+  // Rows are cut into chunks of consecutive rows (so that a tile's variables,
+  // and the S values its lanes gather, stay close together); inside a chunk
+  // BDDs are sorted by hop count and node count, longest first, and every 32
+  // consecutive BDDs form a tile.  Inside a tile everything is interleaved by
+  // lane: slot (h, b) is slot_base + 32 h + b and node number n of lane b is
+  // element 32 n + b of the per-tile arrays.  Node numbers 0 and 1 stand for
+  // the top and bottom terminals, the BDD's own nodes are numbered 2, 3, ...
+  // level by level; child codes are node numbers (8 bits).
+  const int64_t kChunkRows = 16384;
   std::vector<int64_t> order(m);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+    const int64_t cx = x / kChunkRows, cy = y / kChunkRows;
+    if (cx != cy) return cx < cy;
     int64_t kx = R->row_ptr[x + 1] - R->row_ptr[x], ky = R->row_ptr[y + 1] - R->row_ptr[y];
     if (kx != ky) return kx > ky;
     return (P.node_ptr[x + 1] - P.node_ptr[x]) > (P.node_ptr[y + 1] - P.node_ptr[y]);
@@ -265,161 +273,108 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
     max_hops = std::max(max_hops, k);
     P.hop_histogram[std::min(k, 63)]++;
+    if (P.node_ptr[j + 1] - P.node_ptr[j] > kMaxNodesPerBdd)
+      return fail(DG_EINVAL, "dg_plan: row " + std::to_string(j) + " has a BDD of more than " +
+                                 std::to_string(kMaxNodesPerBdd) + " nodes");
   }
   for (uint8_t w : width) max_width = std::max<int>(max_width, w);
 
-  // pass A: decide tile membership
-  struct TileBuild {
-    int64_t first, last;  // range in `order`
-  };
-  std::vector<TileBuild> tb;
-  {
-    std::vector<int> rows_h, used_h;
-    int64_t start = 0;
-    int nh = 0, total_rows = 0, total_slots = 0;
-    auto reset = [&](int64_t s, int hops) {
-      start = s;
-      nh = hops;
-      rows_h.assign(hops, 0);
-      used_h.assign(hops, 0);
-      total_rows = total_slots = 0;
-    };
-    for (int64_t q = 0; q < m; ++q) {
+  const int T = (int)((m + kWarp - 1) / kWarp);
+  // tile t takes BDDs order[32 t .. 32 t + 31]; tiles are then laid out by
+  // shared-memory footprint, largest first, so that tiles of one launch group
+  // are contiguous (and the longest tiles start first)
+  std::vector<int> tile_nh(T, 0), tile_nmax(T, 2), tile_order(T);
+  for (int t = 0; t < T; ++t) {
+    for (int64_t q = (int64_t)t * kWarp; q < std::min<int64_t>(m, (int64_t)(t + 1) * kWarp); ++q) {
       const int64_t j = order[q];
-      const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
-      if (q == 0) reset(0, k);
-      // tentative add
-      int add_rows = 0;
-      for (int h = 0; h < k; ++h) {
-        int w = width[R->row_ptr[j] + h];
-        if (rows_h[h] == 0 || used_h[h] + w > kWarp) add_rows++;
-      }
-      bool fits = total_rows + add_rows <= tile_rows_budget && total_slots + k <= tile_slots;
-      if (!fits && q > start) {
-        tb.push_back({start, q});
-        reset(q, k);
-        add_rows = k;  // every level opens a row in an empty tile
-      }
-      for (int h = 0; h < k; ++h) {
-        int w = width[R->row_ptr[j] + h];
-        if (rows_h[h] == 0 || used_h[h] + w > kWarp) {
-          rows_h[h]++;
-          used_h[h] = w;
-        } else {
-          used_h[h] += w;
-        }
-      }
-      total_rows += add_rows;
-      total_slots += k;
-      (void)nh;
+      tile_nh[t] = std::max<int>(tile_nh[t], (int)(R->row_ptr[j + 1] - R->row_ptr[j]));
+      tile_nmax[t] = std::max<int>(tile_nmax[t], 2 + (int)(P.node_ptr[j + 1] - P.node_ptr[j]));
     }
-    if (m > 0) tb.push_back({start, m});
+    tile_order[t] = t;
   }
-
-  // pass B: lay out every tile
-  const int T = (int)tb.size();
+  std::stable_sort(tile_order.begin(), tile_order.end(), [&](int x, int y) {
+    return sweep_smem_bytes(tile_nmax[x], tile_nh[x], 1) > sweep_smem_bytes(tile_nmax[y], tile_nh[y], 1);
+  });
   P.tiles.resize(T);
   P.slot_to_csr.clear();
   std::vector<int64_t> slot_of_csr(nnz, -1);
-  int64_t row_base = 0, slot_base = 0, hop_base = 0;
+  int64_t node_base = 0, slot_base = 0;
   size_t smem_max = 0, smem_adj_max = 0;
   for (int t = 0; t < T; ++t) {
-    const int64_t q0 = tb[t].first, q1 = tb[t].last;
-    const int nh = (int)(R->row_ptr[order[q0] + 1] - R->row_ptr[order[q0]]);
-    // per hop: layers in BDD order -> rows
-    std::vector<std::vector<int>> layer_row(q1 - q0), layer_lane(q1 - q0);
-    std::vector<int> rows_h(nh, 0), used_h(nh, 0);
-    std::vector<int> nslots_h(nh, 0);
-    int maxw = 1;
-    for (int64_t q = q0; q < q1; ++q) {
-      const int64_t j = order[q];
-      const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
-      layer_row[q - q0].resize(k);
-      layer_lane[q - q0].resize(k);
-      for (int h = 0; h < k; ++h) {
-        int w = width[R->row_ptr[j] + h];
-        maxw = std::max(maxw, w);
-        if (rows_h[h] == 0 || used_h[h] + w > kWarp) {
-          rows_h[h]++;
-          used_h[h] = 0;
-        }
-        layer_row[q - q0][h] = rows_h[h] - 1;
-        layer_lane[q - q0][h] = used_h[h];
-        used_h[h] += w;
-        nslots_h[h]++;
-      }
-    }
-    std::vector<int> row_off(nh + 1, 0), slot_off(nh + 1, 0);
-    for (int h = 0; h < nh; ++h) {
-      row_off[h + 1] = row_off[h] + rows_h[h];
-      slot_off[h + 1] = slot_off[h] + nslots_h[h];
-    }
-    const int nrows = row_off[nh];
-    const int nslots_real = slot_off[nh];
-    const int nslots = (nslots_real + 3) / 4 * 4;
-    if (nrows > 65535 || nslots > 65535) return fail(DG_EINVAL, "dg_plan: a tile exceeds 65535 rows or slots");
+    const int src = tile_order[t];
+    const int64_t q0 = (int64_t)src * kWarp, q1 = std::min<int64_t>(m, q0 + kWarp);
+    const int nb = (int)(q1 - q0);
+    const int nh = tile_nh[src], nmax = tile_nmax[src];
+    const int64_t tslots = (int64_t)nh * kWarp;
     Tile& tile = P.tiles[t];
-    tile.row_base = (int32_t)row_base;
+    tile.node_base = (int32_t)node_base;
     tile.slot_base = (int32_t)slot_base;
-    tile.hop_base = (int32_t)hop_base;
-    tile.nrows = nrows;
-    tile.nslots = nslots;
+    tile.nmax = nmax;
     tile.nhops = nh;
-    tile.maxw = maxw;
-    tile.nbdd = (int32_t)(q1 - q0);
-    for (int h = 0; h <= nh; ++h) P.hoptab.push_back((uint32_t)row_off[h] | ((uint32_t)slot_off[h] << 16));
-    // rows and nodes
-    const size_t rbase = P.rows.size();
-    P.rows.resize(rbase + nrows, RowMeta{0u, 0u});
-    P.lohi.resize((rbase + nrows) * kWarp, 0xFFFFFFFFu);
-    P.slot_var.resize(slot_base + nslots, -1);
-    P.slot_row.resize(slot_base + nslots, -1);
-    P.slot_to_csr.resize(slot_base + nslots, -1);
-    std::vector<int> slot_cursor(nh, 0);
-    for (int64_t q = q0; q < q1; ++q) {
-      const int64_t j = order[q];
+    tile.nbdd = nb;
+    int maxw = 1;
+    P.desc.resize(slot_base + tslots, 0);
+    P.slot_var.resize(slot_base + tslots, -1);
+    P.slot_row.resize(slot_base + tslots, -1);
+    P.slot_to_csr.resize(slot_base + tslots, -1);
+    P.lohi8.resize(node_base + (int64_t)(nmax - 2) * kWarp, 0x0101u);
+    for (int bb = 0; bb < nb; ++bb) {
+      const int64_t j = order[q0 + bb];
       const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
-      const int64_t nb = P.node_ptr[j];
-      int64_t nodes_seen = 0;
+      const int64_t nbj = P.node_ptr[j];
+      int first = 2;
       for (int h = 0; h < k; ++h) {
         const int64_t csr = R->row_ptr[j] + h;
         const int w = width[csr];
-        const int r_local = row_off[h] + layer_row[q - q0][h];
-        const int lane0 = layer_lane[q - q0][h];
-        const int s_local = slot_off[h] + slot_cursor[h]++;
-        RowMeta& rm = P.rows[rbase + r_local];
-        if (rm.head == 0u) rm.info = (uint32_t)s_local;  // first layer of the row
-        rm.head |= 1u << lane0;
-        rm.info = (rm.info & 0xFFFFu) | ((uint32_t)(lane0 + w) << 16);
-        const int64_t as = slot_base + s_local;
-        P.slot_var[as] = R->col[csr];
-        P.slot_row[as] = (int32_t)j;
-        P.slot_to_csr[as] = csr;
-        slot_of_csr[csr] = as;
+        maxw = std::max(maxw, w);
+        const int64_t sl = slot_base + (int64_t)h * kWarp + bb;
+        P.desc[sl] = (uint16_t)(first | (w << 8));
+        P.slot_var[sl] = R->col[csr];
+        P.slot_row[sl] = (int32_t)j;
+        P.slot_to_csr[sl] = csr;
+        slot_of_csr[csr] = sl;
+        const int first_next = first + w;
         for (int r = 0; r < w; ++r) {
-          const int8_t c0 = P.lo8[nb + nodes_seen + r], c1 = P.hi8[nb + nodes_seen + r];
-          auto child = [&](int8_t cc) -> uint32_t {
-            if (cc == kCodeBot) return kBot;
-            if (cc == kCodeTop) return kTop;
-            const int rr = row_off[h + 1] + layer_row[q - q0][h + 1];
-            return (uint32_t)(rr * kWarp + layer_lane[q - q0][h + 1] + cc);
+          auto code = [&](int8_t cc) -> uint32_t {
+            return cc == kCodeBot ? kBotCode : (cc == kCodeTop ? kTopCode : (uint32_t)(first_next + cc));
           };
-          P.lohi[(rbase + r_local) * kWarp + lane0 + r] = child(c0) | (child(c1) << 16);
+          const int64_t nidx = nbj + (first - 2) + r;
+          P.lohi8[node_base + (int64_t)(first - 2 + r) * kWarp + bb] =
+              (uint16_t)(code(P.lo8[nidx]) | (code(P.hi8[nidx]) << 8));
         }
-        nodes_seen += w;
+        first = first_next;
       }
     }
-    smem_max = std::max(smem_max, sweep_smem_bytes(nrows, nslots, nh));
-    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nrows, nslots, nh));
-    P.max_tile_rows = std::max(P.max_tile_rows, nrows);
-    P.max_tile_slots = std::max(P.max_tile_slots, nslots);
+    tile.maxw = maxw;
+    smem_max = std::max(smem_max, sweep_smem_bytes(nmax, nh, 1));
+    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nmax, nh));
+    P.max_tile_rows = std::max(P.max_tile_rows, nmax);
+    P.max_tile_slots = std::max<int32_t>(P.max_tile_slots, (int32_t)tslots);
     P.max_tile_hops = std::max(P.max_tile_hops, nh);
-    row_base += nrows;
-    slot_base += nslots;
-    hop_base += nh + 1;
+    node_base += (int64_t)(nmax - 2) * kWarp;
+    slot_base += tslots;
+  }
+  // launch groups: consecutive tiles whose footprints stay within 1/kGroupRatio
+  // of the group's largest one
+  {
+    const double kGroupRatio = 0.75;
+    int32_t t0 = 0;
+    size_t gmax = 0, gmax0 = 0;
+    for (int t = 0; t < T; ++t) {
+      const size_t r = sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1);
+      if (t > t0 && (double)r < kGroupRatio * (double)gmax) {
+        P.groups.push_back({t0, t, (int32_t)gmax, (int32_t)gmax0});
+        t0 = t;
+        gmax = 0;
+        gmax0 = 0;
+      }
+      gmax = std::max(gmax, r);
+      gmax0 = std::max(gmax0, sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0));
+    }
+    if (T > 0) P.groups.push_back({t0, T, (int32_t)gmax, (int32_t)gmax0});
   }
   const int64_t num_slots = slot_base;
-  if (num_slots >= (int64_t)INT32_MAX || row_base * kWarp >= (int64_t)INT32_MAX)
+  if (num_slots >= (int64_t)INT32_MAX || node_base >= (int64_t)INT32_MAX)
     return fail(DG_EINVAL, "dg_plan: arena exceeds 2^31 slots or nodes");
 
   // ---- 3. variable CSR (slots of each variable, rows ascending) -----------
@@ -460,9 +415,8 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     return at;
   };
   P.off.tiles = put(P.tiles.size() * sizeof(Tile));
-  P.off.hoptab = put(P.hoptab.size() * 4);
-  P.off.rows = put(P.rows.size() * sizeof(RowMeta));
-  P.off.lohi = put(P.lohi.size() * 4);
+  P.off.desc = put(P.desc.size() * 2);
+  P.off.lohi8 = put(P.lohi8.size() * 2);
   P.off.slot_var = put(num_slots * 4);
   P.off.slot_row = put(num_slots * 4);
   P.off.var_ptr = put((size_t)(n + 1) * 4);
@@ -474,6 +428,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.lb_chunks = put((size_t)num_chunks * 16);
   P.off.inst_chunk_ptr = put((size_t)(ni + 1) * 4);
   P.off.S = put((size_t)n * 4);
+  P.off.Sbar = put((size_t)n * 4);
   P.off.E = put((size_t)m * 4);
   P.off.lb_part = put((size_t)num_chunks * 8);
   P.off.total = o;
@@ -485,7 +440,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   z.num_slots = num_slots;
   z.num_lambda = nnz;
   z.num_nodes = num_nodes;
-  z.num_nodes_padded = row_base * kWarp;
+  z.num_nodes_padded = node_base;
   z.n = n;
   z.m = m;
   z.num_inst = ni;
@@ -493,6 +448,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   z.max_hops = max_hops;
   z.max_width = max_width;
   z.smem_bytes = P.smem_sweep;
+  z.num_launch_groups = (int32_t)P.groups.size();
   return DG_OK;
 }
 

@@ -13,41 +13,36 @@
 
 namespace dg {
 
-// Child codes of a node inside a tile (16-bit tile-local node index or a
-// terminal).
-constexpr uint32_t kBot = 0xFFFFu;
-constexpr uint32_t kTop = 0xFFFEu;
+// Node numbers inside a BDD: 0 is the top terminal, 1 the bottom terminal,
+// the BDD's own nodes are 2, 3, ... level by level (at most kMaxNodesPerBdd).
+// A node's children are stored as node numbers (8 bits each).
+constexpr uint32_t kTopCode = 0u;
+constexpr uint32_t kBotCode = 1u;
+constexpr int kMaxNodesPerBdd = 254;
 constexpr int kWarp = 32;
-constexpr int kMaxWidth = 32;  // nodes of one BDD level; a level is one warp segment
+constexpr int kMaxWidth = 32;  // nodes of one BDD level
 
-// One tile = the BDDs one CTA sweeps.  Its nodes are stored hop-major in warp
-// rows of 32 lanes; a BDD level ("layer", one Lagrange slot) never straddles
-// two rows.  Slots are hop-major in the same order as the layers.
+// One tile = up to 32 BDDs swept by one warp, BDD b by lane b.  Per-tile
+// arrays are interleaved by lane: slot (h, b) is slot_base + 32 h + b (its
+// descriptor holds the first node number of level h and the level's width, 0
+// when BDD b has no level h) and node n >= 2 of lane b has its child codes at
+// node_base + 32 (n - 2) + b.
 struct Tile {
-  int32_t row_base;   // first global warp row (node base = 32 * row_base)
-  int32_t slot_base;  // first arena slot (multiple of 4)
-  int32_t hop_base;   // offset of the tile's hop table (nhops + 1 entries)
-  int32_t nrows;      // warp rows
-  int32_t nslots;     // slots, padded to a multiple of 4
+  int32_t node_base;  // first child-code entry (multiple of 32)
+  int32_t slot_base;  // first slot (multiple of 32)
+  int32_t nmax;       // node numbers per lane, terminals included
   int32_t nhops;      // longest BDD of the tile
-  int32_t maxw;       // widest level of the tile (bounds the segmented min)
-  int32_t nbdd;
+  int32_t nbdd;       // BDDs (lanes in use)
+  int32_t maxw;       // widest level
+  int32_t pad0, pad1;
 };
 static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
-
-// Per warp row: bit l of head marks lane l as the first node of a layer;
-// info = first tile-local slot of the row | (valid lanes << 16).
-struct RowMeta {
-  uint32_t head;
-  uint32_t info;
-};
 
 // Device view of an arena (all pointers inside the caller's buffer).
 struct DevArena {
   const Tile* tiles;
-  const uint32_t* hoptab;   // row_off | slot_off << 16 (tile-local)
-  const RowMeta* rows;
-  const uint32_t* lohi;     // lo | hi << 16 per node
+  const uint16_t* desc;     // per slot: first node number | width << 8
+  const uint16_t* lohi8;    // per node and lane: lo code | hi code << 8
   const int32_t* slot_var;  // variable of a slot, -1 for padding
   const int32_t* slot_row;  // original row of a slot, -1 for padding
   const int32_t* var_ptr;   // CSR over variables: slots of variable i
@@ -59,6 +54,7 @@ struct DevArena {
   const int4* lb_chunks;    // {instance, kind (0 rows, 1 vars), begin, end}
   const int32_t* inst_chunk_ptr;
   float* S;                 // scratch: per-variable sum of M (snapshot)
+  float* Sbar;              // scratch: S_i / |J_i| (the mode-0 averaging term)
   float* E;                 // scratch: E^j per original row
   double* lb_part;          // scratch: one partial sum per lb chunk
   int32_t n;
@@ -69,15 +65,24 @@ struct DevArena {
   int32_t num_lb_chunks;
 };
 
+// Tiles that one kernel launch sweeps: consecutive tiles whose shared-memory
+// footprints are within a fixed ratio, so that a launch's per-warp slice of
+// shared memory (the largest footprint of its tiles) wastes little.
+struct LaunchGroup {
+  int32_t tile0, tile1;
+  int32_t region_bytes;   // per-slot omega staged (mode 1)
+  int32_t region_bytes0;  // without omega (mode 0)
+};
+
 struct Plan {
   // sizes
   dg_sizes sizes{};
   int64_t hop_histogram[64]{};
   // host images of the device arrays
   std::vector<Tile> tiles;
-  std::vector<uint32_t> hoptab;
-  std::vector<RowMeta> rows;
-  std::vector<uint32_t> lohi;
+  std::vector<LaunchGroup> groups;
+  std::vector<uint16_t> desc;
+  std::vector<uint16_t> lohi8;
   std::vector<int32_t> slot_var, slot_row;
   std::vector<int32_t> var_ptr, var_slots;
   std::vector<double> c;
@@ -94,24 +99,27 @@ struct Plan {
   std::vector<int8_t> lo8, hi8;
   // byte offsets of every array inside the arena
   struct Off {
-    size_t tiles, hoptab, rows, lohi, slot_var, slot_row, var_ptr, var_slots, c, invdeg, inst_row_ptr, inst_var_ptr,
-        lb_chunks, inst_chunk_ptr, S, E, lb_part, total;
+    size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, c, invdeg, inst_row_ptr, inst_var_ptr,
+        lb_chunks, inst_chunk_ptr, S, Sbar, E, lb_part, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels
   size_t smem_adjoint = 0; // dynamic smem of the adjoint kernels
   int32_t max_tile_rows = 0, max_tile_slots = 0, max_tile_hops = 0;
 };
 
-// Shared-memory footprint of one tile in the sweep kernels.
-inline size_t sweep_smem_bytes(int nrows, int nslots, int nhops) {
-  size_t nn = (size_t)nrows * kWarp;
-  return nn * 12 + (size_t)nrows * 8 + (size_t)(nhops + 1) * 4 + (size_t)nslots * 16 + 64;
+// Shared-memory footprint of one tile (one warp's slice) in the sweep
+// kernels: two cost arrays of 32 x nmax floats and the child codes of
+// 32 x (nmax - 2) nodes, and per slot its descriptor, lambda, the gathered
+// S term and (mode 1) omega and alpha.
+inline size_t sweep_smem_bytes(int nmax, int nhops, int mode) {
+  size_t b = (size_t)nmax * kWarp * 8 + (size_t)(nmax - 2) * kWarp * 2 + (size_t)nhops * kWarp * (mode ? 18 : 10);
+  return (b + 127) / 128 * 128;
 }
-// ... and in the adjoint kernels (adds per-node adjoints, argmin codes and
-// per-slot recomputed quantities).
-inline size_t adjoint_smem_bytes(int nrows, int nslots, int nhops) {
-  size_t nn = (size_t)nrows * kWarp;
-  return nn * 24 + (size_t)nrows * 8 + (size_t)(nhops + 1) * 4 + (size_t)nslots * 40 + 64;
+// ... and in the adjoint kernels (adds per-node adjoints and per-slot
+// recomputed quantities).
+inline size_t adjoint_smem_bytes(int nmax, int nhops) {
+  size_t b = (size_t)nmax * kWarp * 16 + (size_t)nhops * kWarp * 32;
+  return (b + 127) / 128 * 128;
 }
 
 dg_status build_plan(const dg_rows* rows, const dg_options* opts, Plan& plan);

@@ -21,7 +21,11 @@ struct SweepArgs {
 };
 
 cudaError_t set_sweep_smem_limit(size_t bytes);
-void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, size_t smem, cudaStream_t st);
+// Dynamic shared memory one CTA may use; launchers put fewer warps in a CTA
+// when their tiles need more.
+void set_cta_smem_cap(size_t bytes);
+void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
+                  int num_groups, cudaStream_t st);
 
 // S_i = sum_{k in J_i} M_ik in fixed slot order; with renorm, also
 // lambda_ij += alpha_ij * (c_i - sum_k (lambda_ik + M_ik)) computed in FP64.

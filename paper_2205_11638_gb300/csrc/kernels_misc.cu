@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
     if (RENORM) tot += (double)lam[q] + (double)mk;
   }
   A.S[i] = s;
+  A.Sbar[i] = __ldg(A.invdeg + i) * s;
   if (RENORM && e > b) {
     const double r = A.c[i] - tot;
     const float inv = __ldg(A.invdeg + i);
@@ -75,12 +76,22 @@ __global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
   }
 }
 
-__global__ void k_lb_final(DevArena A, double* lb) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= A.num_inst) return;
+// One CTA per instance sums the instance's chunk partials (strided per
+// thread, then a fixed tree): deterministic for a given layout.
+__global__ void __launch_bounds__(256) k_lb_final(DevArena A, double* lb) {
+  const int k = blockIdx.x;
   double t = 0.0;
-  for (int c = A.inst_chunk_ptr[k]; c < A.inst_chunk_ptr[k + 1]; ++c) t += A.lb_part[c];
-  lb[k] = t;
+  for (int c = A.inst_chunk_ptr[k] + threadIdx.x; c < A.inst_chunk_ptr[k + 1]; c += blockDim.x) t += A.lb_part[c];
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    lb[k] = s;
+  }
 }
 
 __global__ void k_seed_M(DevArena A, float* gM) {
@@ -109,7 +120,7 @@ void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st) {
 
 void launch_lower_bound(const DevArena& A, double* lb, cudaStream_t st) {
   if (A.num_lb_chunks > 0) k_lb_partial<<<A.num_lb_chunks, 256, 0, st>>>(A);
-  k_lb_final<<<(A.num_inst + 127) / 128, 128, 0, st>>>(A, lb);
+  k_lb_final<<<A.num_inst, 256, 0, st>>>(A, lb);
 }
 
 void launch_seed_M(const DevArena& A, float* gM, cudaStream_t st) {

@@ -3,214 +3,188 @@
 // that evaluate min-marginals, subproblem energies and minimising
 // assignments on the same layout.
 //
-// One CTA owns one tile for the whole sweep: the tile's structure and slot
-// state are staged in shared memory, the hop loop runs there (one thread per
-// BDD node of the current hop, one warp segment per BDD level), and only the
-// updated lambda and M go back to global memory.  The shortest-path costs of
-// the direction opposite to the sweep (SP(.,T) for a forward sweep, SP(r,.)
-// for a backward one) are recomputed from lambda inside the CTA instead of
-// being kept in HBM between sweeps; they equal the values the previous sweep
-// left, bit for bit, because the same FP32 operations run on the same inputs.
+// One warp owns one tile (up to 32 BDDs, BDD b on lane b).  The warp stages
+// the tile's slot descriptors, lambda and alpha*S in its slice of shared
+// memory; every lane then runs BlockUpdate level by level on its own BDD (a
+// forward sweep visits B_1..B_u, a backward sweep B_u..B_1) and writes the new
+// lambda and M of each level straight to global memory (the lanes of a warp
+// write 32 consecutive slots).  The shortest-path costs of the direction
+// opposite to the sweep (SP(.,T) for a forward sweep, SP(r,.) for a backward
+// one) are recomputed from lambda in shared memory instead of being kept in
+// HBM between sweeps; they equal the values the previous sweep left, bit for
+// bit, because the same FP32 operations run on the same inputs.
 #include "kernels.h"
 #include "sweep.cuh"
 
 namespace dg {
 
-template <int KIND>
-__global__ void __launch_bounds__(512) k_sweep(DevArena A, SweepArgs a) {
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int region_bytes, int tile0, int tile1) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Tile T = A.tiles[blockIdx.x];
-  TileSmem s = carve(smem, T);
-  load_structure(A, T, s);
-  // slot state
-  {
-    const float4* lam4 = reinterpret_cast<const float4*>(a.lam + T.slot_base);
-    const int4* var4 = reinterpret_cast<const int4*>(A.slot_var + T.slot_base);
-    for (int q = threadIdx.x; q < s.ns / 4; q += blockDim.x) {
-      float4 l = lam4[q];
-      reinterpret_cast<float4*>(s.lam)[q] = l;
-      reinterpret_cast<float4*>(s.M)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (KIND == kFwd || KIND == kBwd) {
-        int4 v = __ldg(var4 + q);
-        int vv[4] = {v.x, v.y, v.z, v.w};
-        float as[4];
-        float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (a.mode == 1) al = __ldg(reinterpret_cast<const float4*>(a.alpha + T.slot_base) + q);
-        float alv[4] = {al.x, al.y, al.z, al.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int var = vv[e];
-          float w = 0.f;
-          if (var >= 0) w = (a.mode == 1 ? alv[e] : __ldg(A.invdeg + var)) * A.S[var];
-          as[e] = w;
-        }
-        reinterpret_cast<float4*>(s.as)[q] = make_float4(as[0], as[1], as[2], as[3]);
-        if (a.mode == 1)
-          reinterpret_cast<float4*>(s.om)[q] = __ldg(reinterpret_cast<const float4*>(a.omega + T.slot_base) + q);
-      }
-    }
-  }
-  __syncthreads();
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = tile0 + blockIdx.x * (blockDim.x >> 5) + warp;
+  if (tile >= tile1) return;  // whole warp leaves; no CTA-wide barrier follows
+  const Tile T = A.tiles[tile];
+  TileSmem s = carve<MODE>(smem + (size_t)warp * region_bytes, T);
+  load_tile<KIND == kFwd || KIND == kBwd, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane);
+  const int64_t sbase = T.slot_base;
 
   if (KIND == kFwd || KIND == kMinMarg) {
     // ---- SP(., T) under lambda at sweep start, then the forward sweep -----
-    pass_cost_to_top(s);
-    init_from_root(s);
-    for (int h = 0; h < s.nhops; ++h) {
-      const int r0 = hop_rows(s.hop, h), r1 = hop_rows(s.hop, h + 1);
-      for (int r = r0 + warp; r < r1; r += nw) {
-        const RowMeta rm = s.meta[r];
-        const bool valid = lane < row_valid(rm);
-        const int v = r * kWarp + lane;
-        const uint32_t lh = valid ? s.lohi[v] : 0xFFFFFFFFu;
-        const uint32_t lo = lh & 0xFFFFu, hi = lh >> 16;
-        const int slot = lane_slot(rm, lane);
-        const float dv = valid ? funord(s.d[v]) : f_inf();
-        float a0 = lo != kBot ? dv + child_cost(s.t, lo) : f_inf();
-        float a1 = hi != kBot ? dv + child_cost(s.t, hi) : f_inf();
-        seg_min2(a0, a1, rm.head, lane, s.wpow);
-        float lnew = 0.f;
-        if (valid && ((rm.head >> lane) & 1u)) {
-          const float l = s.lam[slot];
-          const float m0 = a0, m1 = l + a1;
-          if (KIND == kMinMarg) {
-            s.M[slot] = m0;
-            s.om[slot] = m1;
-            lnew = l;
-          } else {
-            const float om = a.mode == 1 ? s.om[slot] : a.omega0;
-            const float Mn = om * (m1 - m0);
-            lnew = l - Mn + s.as[slot];
-            s.lam[slot] = lnew;
-            s.M[slot] = Mn;
-          }
-        }
-        lnew = __shfl_sync(kFull, lnew, head_lane(rm.head, lane));
-        if (valid && h + 1 < s.nhops) {
-          if (lo < kTop) atomicMin(&s.d[lo], ford(dv));
-          if (hi < kTop) atomicMin(&s.d[hi], ford(dv + lnew));
+    lane_cost_to_top(s, lane);
+    if (KIND == kFwd) wait_gathers();
+    if (desc_width(s.desc[lane]) > 0) DG_D(s, 2) = 0.0f;
+    for (int h = 0; h < s.nh; ++h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) break;
+      const int fn = desc_first(ds);
+      const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
+      const int wn = desc_width(dn), fnn = desc_first(dn);
+      float b0 = f_inf(), b1 = f_inf();
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s, n, lane);
+        const float dv = DG_D(s, n);
+        b0 = fminf(b0, dv + DG_T(s, c & 0xFFu));
+        b1 = fminf(b1, dv + DG_T(s, c >> 8));
+      }
+      const int q = h * kWarp + lane;
+      const float l = s.lam[q];
+      const float m0 = b0, m1 = l + b1;
+      float ln = l;
+      if (KIND == kMinMarg) {
+        a.M[sbase + q] = m0;
+        a.out2[sbase + q] = m1;
+      } else {
+        const float om = MODE == 1 ? s.om[q] : a.omega0;
+        const float Mn = om * (m1 - m0);
+        ln = l - Mn + slot_avg<MODE>(s, q);
+        a.lam[sbase + q] = ln;
+        a.M[sbase + q] = Mn;
+      }
+      if (wn > 0) {
+        for (int r = 0; r < wn; ++r) DG_D(s, fnn + r) = f_inf();
+        for (int r = 0; r < w; ++r) {
+          const int n = fn + r;
+          const uint32_t c = node_code(s, n, lane);
+          const uint32_t lo = c & 0xFFu, hi = c >> 8;
+          const float dv = DG_D(s, n);
+          DG_D(s, lo) = fminf(DG_D(s, lo), dv);  // bottom's d entry is scratch
+          DG_D(s, hi) = fminf(DG_D(s, hi), dv + ln);
         }
       }
-      __syncthreads();
     }
   } else if (KIND == kBwd) {
     // ---- SP(r, .) under lambda at sweep start, then the backward sweep ----
-    pass_cost_from_root(s);
-    for (int h = s.nhops - 1; h >= 0; --h) {
-      const int r0 = hop_rows(s.hop, h), r1 = hop_rows(s.hop, h + 1);
-      for (int r = r0 + warp; r < r1; r += nw) {
-        const RowMeta rm = s.meta[r];
-        const bool valid = lane < row_valid(rm);
-        const int v = r * kWarp + lane;
-        const uint32_t lh = valid ? s.lohi[v] : 0xFFFFFFFFu;
-        const uint32_t lo = lh & 0xFFFFu, hi = lh >> 16;
-        const int slot = lane_slot(rm, lane);
-        const float dv = valid ? funord(s.d[v]) : f_inf();
-        const float tl = lo != kBot ? child_cost(s.t, lo) : f_inf();
-        const float th = hi != kBot ? child_cost(s.t, hi) : f_inf();
-        float a0 = lo != kBot ? dv + tl : f_inf();
-        float a1 = hi != kBot ? dv + th : f_inf();
-        seg_min2(a0, a1, rm.head, lane, s.wpow);
-        float lnew = 0.f;
-        if (valid && ((rm.head >> lane) & 1u)) {
-          const float l = s.lam[slot];
-          const float m0 = a0, m1 = l + a1;
-          const float om = a.mode == 1 ? s.om[slot] : a.omega0;
-          const float Mn = om * (m1 - m0);
-          lnew = l - Mn + s.as[slot];
-          s.lam[slot] = lnew;
-          s.M[slot] = Mn;
-        }
-        lnew = __shfl_sync(kFull, lnew, head_lane(rm.head, lane));
-        if (valid) s.t[v] = fminf(tl, hi != kBot ? lnew + th : f_inf());
+    lane_cost_from_root(s, lane);
+    wait_gathers();
+    for (int h = s.nh - 1; h >= 0; --h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) continue;
+      const int fn = desc_first(ds);
+      float b0 = f_inf(), b1 = f_inf();
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s, n, lane);
+        const float dv = DG_D(s, n);
+        b0 = fminf(b0, dv + DG_T(s, c & 0xFFu));
+        b1 = fminf(b1, dv + DG_T(s, c >> 8));
       }
-      __syncthreads();
+      const int q = h * kWarp + lane;
+      const float l = s.lam[q];
+      const float m0 = b0, m1 = l + b1;
+      const float om = MODE == 1 ? s.om[q] : a.omega0;
+      const float Mn = om * (m1 - m0);
+      const float ln = l - Mn + slot_avg<MODE>(s, q);
+      a.lam[sbase + q] = ln;
+      a.M[sbase + q] = Mn;
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s, n, lane);
+        DG_T(s, n) = fminf(DG_T(s, c & 0xFFu), ln + DG_T(s, c >> 8));
+      }
     }
   } else {
     // kEnergy / kSeed: SP(., T) under lambda
-    pass_cost_to_top(s);
+    lane_cost_to_top(s, lane);
   }
 
   if (KIND == kSeed) {
-    // walk the minimising path from every root: 0-arc on ties
-    for (int v = threadIdx.x; v < s.nn; v += blockDim.x) s.d[v] = v < (int)hop_rows(s.hop, 1) * kWarp ? 1 : 0;
-    __syncthreads();
-    for (int h = 0; h < s.nhops; ++h) {
-      const int r0 = hop_rows(s.hop, h), r1 = hop_rows(s.hop, h + 1);
-      for (int r = r0 + warp; r < r1; r += nw) {
-        const RowMeta rm = s.meta[r];
-        const int v = r * kWarp + lane;
-        if (lane < row_valid(rm) && s.d[v]) {
-          const uint32_t lh = s.lohi[v];
-          const uint32_t lo = lh & 0xFFFFu, hi = lh >> 16;
-          const int slot = lane_slot(rm, lane);
-          bool take0 = false;
-          if (lo != kBot) take0 = hi == kBot || child_cost(s.t, lo) <= s.lam[slot] + child_cost(s.t, hi);
-          s.M[slot] = take0 ? 0.f : 1.f;
-          const uint32_t ch = take0 ? lo : hi;
-          if (ch < kTop) s.d[ch] = 1;
-        }
-      }
-      __syncthreads();
+    // walk the minimising path from my root: 0-arc on ties
+    int n = 2;
+    for (int h = 0; h < s.nh; ++h) {
+      if (desc_width(s.desc[h * kWarp + lane]) == 0) break;
+      const uint32_t c = node_code(s, n, lane);
+      const uint32_t lo = c & 0xFFu, hi = c >> 8;
+      const int q = h * kWarp + lane;
+      const bool take0 = lo != kBotCode && (hi == kBotCode || DG_T(s, lo) <= s.lam[q] + DG_T(s, hi));
+      a.M[sbase + q] = take0 ? 0.f : 1.f;
+      n = (int)(take0 ? lo : hi);
     }
   }
 
-  if ((KIND == kBwd || KIND == kEnergy) && a.E != nullptr) {
-    // hop-0 nodes are the roots; SP(root, T) = E^j
-    const int r1 = hop_rows(s.hop, 1);
-    for (int v = threadIdx.x; v < r1 * kWarp; v += blockDim.x) {
-      const RowMeta rm = s.meta[v >> 5];
-      const int ln = v & 31;
-      if (ln < row_valid(rm)) {
-        const int row = __ldg(A.slot_row + T.slot_base + lane_slot(rm, ln));
-        a.E[row] = s.t[v];
-      }
-    }
-  }
-
-  // write back
-  if (KIND == kFwd || KIND == kBwd) {
-    float4* lam4 = reinterpret_cast<float4*>(a.lam + T.slot_base);
-    float4* M4 = reinterpret_cast<float4*>(a.M + T.slot_base);
-    for (int q = threadIdx.x; q < s.ns / 4; q += blockDim.x) {
-      lam4[q] = reinterpret_cast<const float4*>(s.lam)[q];
-      M4[q] = reinterpret_cast<const float4*>(s.M)[q];
-    }
-  } else if (KIND == kMinMarg) {
-    float4* m0 = reinterpret_cast<float4*>(a.M + T.slot_base);
-    float4* m1 = reinterpret_cast<float4*>(a.out2 + T.slot_base);
-    for (int q = threadIdx.x; q < s.ns / 4; q += blockDim.x) {
-      m0[q] = reinterpret_cast<const float4*>(s.M)[q];
-      m1[q] = reinterpret_cast<const float4*>(s.om)[q];
-    }
-  } else if (KIND == kSeed) {
-    float4* g = reinterpret_cast<float4*>(a.M + T.slot_base);
-    for (int q = threadIdx.x; q < s.ns / 4; q += blockDim.x) g[q] = reinterpret_cast<const float4*>(s.M)[q];
+  if ((KIND == kBwd || KIND == kEnergy) && a.E != nullptr && lane < T.nbdd) {
+    // SP(root, T) = E^j of my BDD
+    const int row = __ldg(A.slot_row + sbase + lane);
+    a.E[row] = DG_T(s, 2);
   }
 }
 
-cudaError_t set_sweep_smem_limit(size_t bytes) {
-  cudaError_t e = cudaSuccess;
-  int b = (int)bytes;
-  if ((e = cudaFuncSetAttribute(k_sweep<kFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(k_sweep<kBwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(k_sweep<kMinMarg>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(k_sweep<kEnergy>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(k_sweep<kSeed>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+template <int KIND>
+static cudaError_t set_attr(int b) {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep<KIND, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
 
-void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, size_t smem, cudaStream_t st) {
-  if (A.num_tiles == 0) return;
-  dim3 grid(A.num_tiles), block(threads);
+cudaError_t set_sweep_smem_limit(size_t bytes) {
+  const int b = (int)bytes;
+  cudaError_t e = set_attr<kFwd>(b);
+  if (e == cudaSuccess) e = set_attr<kBwd>(b);
+  if (e == cudaSuccess) e = set_attr<kMinMarg>(b);
+  if (e == cudaSuccess) e = set_attr<kEnergy>(b);
+  if (e == cudaSuccess) e = set_attr<kSeed>(b);
+  return e;
+}
+
+static size_t g_cta_smem_cap = 227 * 1024;
+void set_cta_smem_cap(size_t bytes) { g_cta_smem_cap = bytes; }
+
+template <int KIND, int MODE>
+static void launch_groups(const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
+                          int num_groups, cudaStream_t st) {
+  for (int g = 0; g < num_groups; ++g) {
+    const LaunchGroup& G = groups[g];
+    const size_t region = (size_t)(MODE == 1 ? G.region_bytes : G.region_bytes0);
+    int wpc = threads / kWarp;
+    if (wpc > 4) wpc = 4;  // __launch_bounds__(128)
+    while (wpc > 1 && region * wpc > g_cta_smem_cap) --wpc;
+    const int nt = G.tile1 - G.tile0;
+    dim3 grid((nt + wpc - 1) / wpc), block(wpc * kWarp);
+    k_sweep<KIND, MODE><<<grid, block, region * wpc, st>>>(A, a, (int)region, G.tile0, G.tile1);
+  }
+}
+
+// One launch per launch group; threads = warps per CTA * 32, every warp
+// sweeps one tile with its own slice of the group's shared memory.  Only
+// the update sweeps read omega/alpha, so only they have a mode-1 variant.
+void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
+                  int num_groups, cudaStream_t st) {
+  const bool m1 = a.mode == 1;
   switch (kind) {
-    case kFwd: k_sweep<kFwd><<<grid, block, smem, st>>>(A, a); break;
-    case kBwd: k_sweep<kBwd><<<grid, block, smem, st>>>(A, a); break;
-    case kMinMarg: k_sweep<kMinMarg><<<grid, block, smem, st>>>(A, a); break;
-    case kEnergy: k_sweep<kEnergy><<<grid, block, smem, st>>>(A, a); break;
-    default: k_sweep<kSeed><<<grid, block, smem, st>>>(A, a); break;
+    case kFwd:
+      m1 ? launch_groups<kFwd, 1>(A, a, threads, groups, num_groups, st)
+         : launch_groups<kFwd, 0>(A, a, threads, groups, num_groups, st);
+      break;
+    case kBwd:
+      m1 ? launch_groups<kBwd, 1>(A, a, threads, groups, num_groups, st)
+         : launch_groups<kBwd, 0>(A, a, threads, groups, num_groups, st);
+      break;
+    case kMinMarg: launch_groups<kMinMarg, 0>(A, a, threads, groups, num_groups, st); break;
+    case kEnergy: launch_groups<kEnergy, 0>(A, a, threads, groups, num_groups, st); break;
+    default: launch_groups<kSeed, 0>(A, a, threads, groups, num_groups, st); break;
   }
 }
 

@@ -1,6 +1,14 @@
 // sweep.cuh -- device building blocks shared by the sweep, min-marginal and
-// adjoint kernels: shared-memory tile staging, warp-segmented reductions over
-// BDD levels and the per-hop min-sum passes.
+// adjoint kernels: per-warp shared-memory staging of one tile and the
+// per-lane min-sum passes over one BDD.
+//
+// Execution model: one warp owns one tile of up to 32 BDDs and lane b owns
+// BDD b.  A lane walks its BDD level by level (App. B: SP(root, v) and
+// SP(v, top) by min-sum over the 0- and 1-arcs).  Everything a tile holds is
+// interleaved by lane (element 32 n + b belongs to lane b), so the 32 lanes of
+// a warp always touch 32 different shared-memory banks and read global memory
+// in coalesced segments.  Node numbers 0 and 1 are the top (cost 0) and
+// bottom (cost +inf) terminals, so arcs into terminals need no branch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,174 +18,168 @@
 
 namespace dg {
 
-constexpr unsigned kFull = 0xFFFFFFFFu;
-
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
-// Monotone map float -> int so that shared-memory atomicMin on ints is a min
-// on floats (no NaNs occur: bottom arcs are skipped, never added).
-__device__ __forceinline__ int ford(float f) {
-  int i = __float_as_int(f);
-  return i >= 0 ? i : i ^ 0x7FFFFFFF;
-}
-__device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+__device__ __forceinline__ int desc_width(uint32_t ds) { return (int)(ds >> 8); }
+__device__ __forceinline__ int desc_first(uint32_t ds) { return (int)(ds & 0xFFu); }
 
-__device__ __forceinline__ unsigned lanemask_le(int lane) { return kFull >> (31 - lane); }
-
-// Lane of the first node of my level inside the warp row.
-__device__ __forceinline__ int head_lane(unsigned head, int lane) { return 31 - __clz(head & lanemask_le(lane)); }
-
-// Tile-local slot of the level my lane belongs to.
-__device__ __forceinline__ int lane_slot(const RowMeta& rm, int lane) {
-  return (int)(rm.info & 0xFFFFu) + __popc(rm.head & lanemask_le(lane)) - 1;
-}
-__device__ __forceinline__ int row_valid(const RowMeta& rm) { return (int)(rm.info >> 16); }
-
-// Segmented min towards the first lane of every level: after the call the
-// head lane of a level holds the min over the level's lanes.  `width_pow`
-// bounds the level width (power of two >= widest level of the tile).
-__device__ __forceinline__ void seg_min2(float& a, float& b, unsigned head, int lane, int width_pow) {
-  const unsigned long long hm = (unsigned long long)head | (1ull << 32);
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    if (off >= width_pow) break;
-    float oa = __shfl_down_sync(kFull, a, off);
-    float ob = __shfl_down_sync(kFull, b, off);
-    unsigned long long between = (hm >> (lane + 1)) & ((1ull << off) - 1ull);
-    if (between == 0ull) {
-      a = fminf(a, oa);
-      b = fminf(b, ob);
-    }
-  }
-}
-
-// Segmented sum towards the head lane (same segments as seg_min2); the sum
-// order is fixed by the layout, so the result is deterministic.
-__device__ __forceinline__ float seg_sum(float a, unsigned head, int lane, int width_pow) {
-  const unsigned long long hm = (unsigned long long)head | (1ull << 32);
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    if (off >= width_pow) break;
-    float o = __shfl_down_sync(kFull, a, off);
-    unsigned long long between = (hm >> (lane + 1)) & ((1ull << off) - 1ull);
-    if (between == 0ull) a += o;
-  }
-  return a;
-}
-
-__device__ __forceinline__ int pow2_ceil(int w) {
-  int p = 1;
-  while (p < w) p <<= 1;
-  return p;
-}
-
-__device__ __forceinline__ uint32_t hop_rows(const uint32_t* s_hop, int h) { return s_hop[h] & 0xFFFFu; }
-__device__ __forceinline__ uint32_t hop_slots(const uint32_t* s_hop, int h) { return s_hop[h] >> 16; }
-
-// Shared-memory image of one tile.
+// Shared-memory image of one tile (one warp's slice).
 struct TileSmem {
-  uint32_t* lohi;  // [nn]
-  float* t;        // [nn] SP(v, top)
-  int* d;          // [nn] SP(root, v) as ordered ints
-  RowMeta* meta;   // [nrows]
-  uint32_t* hop;   // [nhops + 1]
-  float* lam;      // [ns]
-  float* as;       // [ns] alpha_ij * S_i  (sweeps) / scratch
-  float* M;        // [ns] M out / m0 / seeds
-  float* om;       // [ns] omega per slot (mode 1) / m1
-  int nn, ns, nrows, nhops, wpow;
+  float* t;        // [32 * nmax] SP(v, top), lane-interleaved
+  float* d;        // [32 * nmax] SP(root, v), lane-interleaved
+  float* lam;      // [32 * nh]
+  float* sg;       // [32 * nh] variable of the slot, then the gathered S term
+  float* om;       // [32 * nh] omega_ij (mode 1)
+  float* al;       // [32 * nh] alpha_ij (mode 1)
+  uint16_t* desc;  // [32 * nh]
+  uint16_t* code;  // [32 * (nmax - 2)] child codes (lo | hi << 8), lane-interleaved
+  int nmax, nh;
 };
 
-__device__ __forceinline__ TileSmem carve(unsigned char* smem, const Tile& T) {
+template <int MODE>
+__device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
   TileSmem s;
-  s.nn = T.nrows * kWarp;
-  s.ns = T.nslots;
-  s.nrows = T.nrows;
-  s.nhops = T.nhops;
-  s.wpow = pow2_ceil(T.maxw);
-  unsigned char* p = smem;
-  s.lohi = (uint32_t*)p;
-  p += (size_t)s.nn * 4;
+  s.nmax = T.nmax;
+  s.nh = T.nhops;
+  const int ns = s.nh * kWarp;
   s.t = (float*)p;
-  p += (size_t)s.nn * 4;
-  s.d = (int*)p;
-  p += (size_t)s.nn * 4;
+  p += (size_t)s.nmax * kWarp * 4;
+  s.d = (float*)p;
+  p += (size_t)s.nmax * kWarp * 4;
   s.lam = (float*)p;
-  p += (size_t)s.ns * 4;
-  s.as = (float*)p;
-  p += (size_t)s.ns * 4;
-  s.M = (float*)p;
-  p += (size_t)s.ns * 4;
-  s.om = (float*)p;
-  p += (size_t)s.ns * 4;
-  s.meta = (RowMeta*)p;
-  p += (size_t)s.nrows * 8;
-  s.hop = (uint32_t*)p;
+  p += (size_t)ns * 4;
+  s.sg = (float*)p;
+  p += (size_t)ns * 4;
+  if (MODE == 1) {
+    s.om = (float*)p;
+    p += (size_t)ns * 4;
+    s.al = (float*)p;
+    p += (size_t)ns * 4;
+  } else {
+    s.om = s.al = nullptr;
+  }
+  s.desc = (uint16_t*)p;
+  p += (size_t)ns * 2;
+  s.code = (uint16_t*)p;
   return s;
 }
 
-// Stages the structure of tile T (child indices, row metadata, hop table).
-__device__ __forceinline__ void load_structure(const DevArena& A, const Tile& T, TileSmem& s) {
-  const uint4* src = reinterpret_cast<const uint4*>(A.lohi + (size_t)T.row_base * kWarp);
-  uint4* dst = reinterpret_cast<uint4*>(s.lohi);
-  for (int i = threadIdx.x; i < s.nn / 4; i += blockDim.x) dst[i] = __ldg(src + i);
-  const uint2* msrc = reinterpret_cast<const uint2*>(A.rows + T.row_base);
-  uint2* mdst = reinterpret_cast<uint2*>(s.meta);
-  for (int i = threadIdx.x; i < s.nrows; i += blockDim.x) mdst[i] = __ldg(msrc + i);
-  for (int i = threadIdx.x; i <= s.nhops; i += blockDim.x) s.hop[i] = __ldg(A.hoptab + T.hop_base + i);
+// Cost arrays of lane `lane`: element of node number n.
+#define DG_T(s, n) (s).t[(n) * kWarp + lane]
+#define DG_D(s, n) (s).d[(n) * kWarp + lane]
+
+// Child codes (lo | hi << 8) of node number n >= 2 of my BDD.
+__device__ __forceinline__ uint32_t node_code(const TileSmem& s, int n, int lane) {
+  return s.code[(n - 2) * kWarp + lane];
 }
 
-__device__ __forceinline__ float child_cost(const float* t, uint32_t c) {
-  return c == kTop ? 0.0f : t[c];
+// Asynchronous global -> shared copies (cp.async): 16 B for the streamed
+// tile arrays, 4 B for the gathers of per-variable terms.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes, int lane) {
+  char* d = reinterpret_cast<char*>(dst);
+  const char* g = reinterpret_cast<const char*>(src);
+  for (int o = lane * 16; o < bytes; o += kWarp * 16) cp_async16(d + o, g + o);
 }
 
-// SP(v, top) for every node of the tile under s.lam (levels bottom-up).
-__device__ __forceinline__ void pass_cost_to_top(TileSmem& s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int h = s.nhops - 1; h >= 0; --h) {
-    const int r0 = hop_rows(s.hop, h), r1 = hop_rows(s.hop, h + 1);
-    for (int r = r0 + warp; r < r1; r += nw) {
-      const RowMeta rm = s.meta[r];
-      if (lane < row_valid(rm)) {
-        const int v = r * kWarp + lane;
-        const uint32_t lh = s.lohi[v];
-        const uint32_t lo = lh & 0xFFFFu, hi = lh >> 16;
-        float best = f_inf();
-        if (lo != kBot) best = child_cost(s.t, lo);
-        if (hi != kBot) best = fminf(best, s.lam[lane_slot(rm, lane)] + child_cost(s.t, hi));
-        s.t[v] = best;
-      }
+// Warp-cooperative staging of the tile: child codes, slot descriptors,
+// lambda and (mode 1) omega and alpha, all by asynchronous copies.  With
+// WITH_S the per-variable averaging term (S_i / |J_i| in mode 0, S_i in
+// mode 1) of every slot is gathered too; those copies stay in flight until
+// wait_gathers(), so callers overlap them with the first min-sum pass.
+template <bool WITH_S, int MODE>
+__device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, TileSmem& s, const float* lam,
+                                          const float* omega, const float* alpha, int lane) {
+  const int ns = s.nh * kWarp;
+  copy_async(s.code, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+  copy_async(s.desc, A.desc + T.slot_base, ns * 2, lane);
+  copy_async(s.lam, lam + T.slot_base, ns * 4, lane);
+  if (WITH_S) {
+    copy_async(s.sg, A.slot_var + T.slot_base, ns * 4, lane);
+    if (MODE == 1) {
+      copy_async(s.om, omega + T.slot_base, ns * 4, lane);
+      copy_async(s.al, alpha + T.slot_base, ns * 4, lane);
     }
-    __syncthreads();
+  }
+  cp_async_commit();
+  DG_T(s, kTopCode) = 0.0f;
+  DG_T(s, kBotCode) = f_inf();
+  cp_async_wait_all();
+  __syncwarp();
+  if (WITH_S) {
+    const float* src = MODE == 1 ? A.S : A.Sbar;
+    int* sv = reinterpret_cast<int*>(s.sg);
+#pragma unroll 4
+    for (int q = lane; q < ns; q += kWarp) {
+      const int v = sv[q];
+      if (v >= 0)
+        cp_async4(s.sg + q, src + v);
+      else
+        s.sg[q] = 0.0f;
+    }
+    cp_async_commit();
   }
 }
 
-// d = ordered(+inf) everywhere, 0 at the roots (the nodes of hop 0).
-__device__ __forceinline__ void init_from_root(TileSmem& s) {
-  const int nroot = hop_rows(s.hop, 1) * kWarp;
-  const int zero = ford(0.0f), inf = ford(f_inf());
-  for (int v = threadIdx.x; v < s.nn; v += blockDim.x) s.d[v] = v < nroot ? zero : inf;
-  __syncthreads();
+// Completes the gathers issued by load_tile<true>.
+__device__ __forceinline__ void wait_gathers() {
+  cp_async_wait_all();
+  __syncwarp();
 }
 
-// SP(root, v) for every node under s.lam (levels top-down, push relaxation).
-__device__ __forceinline__ void pass_cost_from_root(TileSmem& s) {
-  init_from_root(s);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int h = 0; h + 1 < s.nhops; ++h) {
-    const int r0 = hop_rows(s.hop, h), r1 = hop_rows(s.hop, h + 1);
-    for (int r = r0 + warp; r < r1; r += nw) {
-      const RowMeta rm = s.meta[r];
-      if (lane < row_valid(rm)) {
-        const int v = r * kWarp + lane;
-        const uint32_t lh = s.lohi[v];
-        const uint32_t lo = lh & 0xFFFFu, hi = lh >> 16;
-        const float dv = funord(s.d[v]);
-        if (lo < kTop) atomicMin(&s.d[lo], ford(dv));
-        if (hi < kTop) atomicMin(&s.d[hi], ford(dv + s.lam[lane_slot(rm, lane)]));
-      }
+// alpha_ij * S_i of slot q (after wait_gathers).
+template <int MODE>
+__device__ __forceinline__ float slot_avg(const TileSmem& s, int q) {
+  return MODE == 1 ? s.al[q] * s.sg[q] : s.sg[q];
+}
+
+// SP(v, top) of every node of my BDD under s.lam (levels bottom-up).
+__device__ __forceinline__ void lane_cost_to_top(TileSmem& s, int lane) {
+  for (int h = s.nh - 1; h >= 0; --h) {
+    const uint32_t ds = s.desc[h * kWarp + lane];
+    const int w = desc_width(ds);
+    if (w == 0) continue;
+    const int fn = desc_first(ds);
+    const float l = s.lam[h * kWarp + lane];
+    for (int r = 0; r < w; ++r) {
+      const int n = fn + r;
+      const uint32_t c = node_code(s, n, lane);
+      DG_T(s, n) = fminf(DG_T(s, c & 0xFFu), l + DG_T(s, c >> 8));
     }
-    __syncthreads();
+  }
+}
+
+// SP(root, v) of every node of my BDD under s.lam (levels top-down).
+__device__ __forceinline__ void lane_cost_from_root(TileSmem& s, int lane) {
+  if (desc_width(s.desc[lane]) == 0) return;
+  DG_D(s, 2) = 0.0f;
+  for (int h = 0; h + 1 < s.nh; ++h) {
+    const uint32_t ds = s.desc[h * kWarp + lane];
+    const uint32_t dn = s.desc[(h + 1) * kWarp + lane];
+    const int w = desc_width(ds), wn = desc_width(dn);
+    if (wn == 0) break;
+    const int fn = desc_first(ds), fnn = desc_first(dn);
+    const float l = s.lam[h * kWarp + lane];
+    for (int r = 0; r < wn; ++r) DG_D(s, fnn + r) = f_inf();
+    for (int r = 0; r < w; ++r) {
+      const int n = fn + r;
+      const uint32_t c = node_code(s, n, lane);
+      const uint32_t lo = c & 0xFFu, hi = c >> 8;
+      const float dv = DG_D(s, n);
+      // arcs into the bottom terminal write its unused d entry
+      DG_D(s, lo) = fminf(DG_D(s, lo), dv);
+      DG_D(s, hi) = fminf(DG_D(s, hi), dv + l);
+    }
   }
 }
 
