@@ -200,6 +200,22 @@ dg_status dg_min_marginals(dg_arena* arena, void* stream, const float* lam, floa
 dg_status dg_lower_bound(dg_arena* arena, void* stream, const float* lam, const float* M, double* lb_per_inst,
                          float* E_per_row);
 
+/* The bound of dg_lower_bound (float64[num_inst] in lb_per_inst) for callers
+ * that cannot hand the library any scratch memory, e.g. code inside a stream
+ * capture that forbids allocation or an embedder with a fixed device-memory
+ * budget.  The paper has no counterpart: this is a deployment variant.  Its
+ * intermediates (E^j per row, S_i and S_i/|J_i| per variable, one partial sum
+ * per reduction chunk) live in a static device array of 4 MiB inside libdg
+ * instead of the arena's scratch area; the call allocates nothing (no
+ * cudaMalloc, no allocating library routine).  Arenas needing more than
+ * 4 m + 8 n + 8 * chunks <= 4 MiB get DG_EINVAL.  Every GPU that loads libdg
+ * holds the array until exit; all calls share it, so calls that overlap on
+ * the GPU race (calls ordered on one stream are safe).  The first call on a
+ * device looks up the array's device address; make it before any stream
+ * capture. */
+dg_status dg_lower_bound_noalloc(dg_arena* arena, void* stream, const float* lam, const float* M,
+                                 double* lb_per_inst);
+
 /* Gradient of the lower bound (eq. 3 plus the unary term) at (lam, M):
  * g_lam = minimising assignment of every BDD (0-arc on ties),
  * g_M_ij = [S_i < 0]. */

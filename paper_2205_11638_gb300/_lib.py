@@ -71,6 +71,7 @@ SIGNATURES = {
     "dg_min_marginals": (c_int32, [P, P, P, P, P]),
     "dg_lower_bound": (c_int32, [P, P, P, P, P, P]),
     "dg_lb_seed": (c_int32, [P, P, P, P, P, P]),
+    "dg_lower_bound_noalloc": (c_int32, [P, P, P, P, P]),
     "dg_backward_workspace_bytes": (c_size_t, [P, c_int32, c_int32]),
     "dg_backward": (c_int32, [P, P, P, P, P, P, c_int32, c_int32, c_int32, P, P, P, P, P, P, P, c_size_t,
                               ctypes.POINTER(dg_options)]),

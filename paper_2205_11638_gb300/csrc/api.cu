@@ -381,6 +381,14 @@ dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const flo
   return check_launch("dg_lower_bound");
 }
 
+dg_status dg_lower_bound_noalloc(dg_arena* ar, void* stream, const float* lam, const float* M, double* lb) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M || !lb) return fail(DG_EINVAL, "dg_lower_bound_noalloc: null pointer");
+  if (dg_status s = check_vectors("dg_lower_bound_noalloc", lam, M)) return s;
+  return lower_bound_noalloc(ar->dev, ar->groups.data(), (int)ar->groups.size(), threads_of(nullptr),
+                             (cudaStream_t)stream, lam, M, lb);
+}
+
 dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* M, float* g_lam, float* g_M) {
   if (dg_status s = check_state(ar)) return s;
   if (!lam || !M || !g_lam || !g_M) return fail(DG_EINVAL, "dg_lb_seed: null pointer");

@@ -36,4 +36,8 @@ void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st);
 void launch_lower_bound(const DevArena& A, double* lb_out, cudaStream_t st);
 void launch_seed_M(const DevArena& A, float* g_M, cudaStream_t st);
 
+// dg_lower_bound with its intermediates in a static device array (noalloc.cu).
+dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, int num_groups, int threads,
+                              cudaStream_t st, const float* lam, const float* M, double* lb);
+
 }  // namespace dg

@@ -216,6 +216,15 @@ class Arena:
               "dg_lower_bound")
         return (lb, E) if energies else lb
 
+    def lower_bound_noalloc(self, lam, M, out=None, stream=None):
+        """dg_lower_bound_noalloc: the bound with libdg's static scratch; ``out``
+        (float64[num_inst] on the device) may be passed in by callers that
+        manage their own memory."""
+        lb = out if out is not None else torch.zeros(self.num_inst, dtype=torch.float64, device=self.device)
+        check(_lib.load().dg_lower_bound_noalloc(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(lb)),
+              "dg_lower_bound_noalloc")
+        return lb
+
     def lb_seed(self, lam, M, stream=None):
         gl, gM = self.zeros(), self.zeros()
         check(_lib.load().dg_lb_seed(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(gl), _ptr(gM)),
