@@ -28,6 +28,8 @@ using namespace dg;
 struct dg_arena_s {
   DevArena dev{};
   std::vector<LaunchGroup> groups;
+  std::vector<AdjGroup> adj_groups;
+  size_t cta_smem_cap = 0;
   dg_sizes sizes{};
   dg_stats stats{};
   size_t smem_sweep = 0, smem_adjoint = 0;
@@ -226,11 +228,17 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
     if (e != cudaSuccess) return cuda_fail(e, "dg_bind: device attribute");
     if ((size_t)optin < P.smem_sweep) return fail(DG_EINVAL, "dg_bind: tiles need more shared memory than a CTA has");
     e = set_sweep_smem_limit((size_t)optin);  // same limit for every arena of the process
+    if (e == cudaSuccess) e = set_adjoint_smem_limit((size_t)optin);
     set_cta_smem_cap((size_t)optin);
     if (e != cudaSuccess) return cuda_fail(e, "dg_bind: shared-memory limit");
   }
   dg_arena* ar = new dg_arena();
   cudaGetDevice(&ar->device);
+  {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ar->device);
+    ar->cta_smem_cap = (size_t)optin;
+  }
   char* b = (char*)arena_dev;
   DevArena& A = ar->dev;
   A.tiles = (const Tile*)(b + P.off.tiles);
@@ -259,6 +267,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   ar->sizes = P.sizes;
   ar->smem_sweep = P.smem_sweep;
   ar->groups = P.groups;
+  ar->adj_groups = P.adj_groups;
   ar->smem_adjoint = P.smem_adjoint;
   ar->max_tile_rows = P.max_tile_rows;
   ar->max_tile_slots = P.max_tile_slots;
@@ -450,21 +459,152 @@ void dg_graph_destroy(dg_graph_t* g) {
   delete g;
 }
 
+namespace {
+
+struct BwdLayout {
+  size_t ck_lam, ck_M, seg_lam, seg_S, w_lam, w_M, sdot, sd_a, sd_b, total;
+  int nseg, k;
+};
+
+BwdLayout backward_layout(const dg_arena* ar, int iters, int ckpt_every) {
+  BwdLayout L{};
+  const size_t NS = (size_t)ar->sizes.num_slots, n = (size_t)ar->sizes.n;
+  L.k = ckpt_every > 0 ? std::min(ckpt_every, std::max(iters, 1)) : std::max(iters, 1);
+  L.nseg = iters > 0 ? (iters + L.k - 1) / L.k : 0;
+  size_t o = 0;
+  auto put = [&](size_t bytes) {
+    size_t at = o;
+    o = (o + bytes + 255) / 256 * 256;
+    return at;
+  };
+  L.ck_lam = put((size_t)L.nseg * NS * 4);
+  L.ck_M = put((size_t)L.nseg * NS * 4);
+  L.seg_lam = put((size_t)2 * L.k * NS * 4);
+  L.seg_S = put((size_t)2 * L.k * n * 4);
+  L.w_lam = put(NS * 4);
+  L.w_M = put(NS * 4);
+  L.sdot = put(NS * 4);
+  L.sd_a = put(n * 4);
+  L.sd_b = put(n * 4);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
 size_t dg_backward_workspace_bytes(const dg_arena* ar, int32_t iters, int32_t ckpt_every) {
-  (void)ar;
-  (void)iters;
-  (void)ckpt_every;
-  return 0;
+  if (!ar || iters < 0) return 0;
+  return backward_layout(ar, iters, ckpt_every).total;
 }
 
 dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float* M0, const float* omega,
                       const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
                       const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha, void* workspace,
                       size_t ws_bytes, const dg_options* opts) {
-  (void)ar; (void)stream; (void)lam0; (void)M0; (void)omega; (void)alpha; (void)mode; (void)iters;
-  (void)ckpt_every; (void)g_lam_T; (void)g_M_T; (void)g_lam0; (void)g_M0; (void)g_omega; (void)g_alpha;
-  (void)workspace; (void)ws_bytes; (void)opts;
-  return fail(DG_ESTATE, "dg_backward: not available in this build");
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam0 || !M0 || !g_lam_T || !g_M_T || !g_lam0 || !g_M0 || !g_omega || !g_alpha)
+    return fail(DG_EINVAL, "dg_backward: null pointer");
+  if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_backward: mode must be 0 or 1");
+  if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_backward: mode 1 needs omega and alpha");
+  if (iters < 0) return fail(DG_EINVAL, "dg_backward: negative iteration count");
+  if (dg_status s = check_vectors("dg_backward", lam0, M0, omega, alpha)) return s;
+  if (dg_status s = check_vectors("dg_backward", g_lam_T, g_M_T, g_lam0, g_M0)) return s;
+  if (dg_status s = check_vectors("dg_backward", g_omega, g_alpha)) return s;
+  for (const AdjGroup& g : ar->adj_groups)
+    if ((size_t)(mode ? g.region1 : g.region0) > ar->cta_smem_cap)
+      return fail(DG_EINVAL, "dg_backward: a tile's adjoint state does not fit one CTA's shared memory");
+  const BwdLayout L = backward_layout(ar, iters, ckpt_every);
+  if (iters > 0 && (!workspace || ws_bytes < L.total))
+    return fail(DG_EINVAL, "dg_backward: workspace smaller than dg_backward_workspace_bytes()");
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevArena& A = ar->dev;
+  const size_t NS = (size_t)ar->sizes.num_slots, n = (size_t)ar->sizes.n;
+  const size_t bNS = NS * 4, bn = n * 4;
+  cudaError_t e = cudaSuccess;
+  auto cpy = [&](void* d, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  e = cudaMemsetAsync(g_omega, 0, bNS, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g_alpha, 0, bNS, st);
+  if (iters == 0) {
+    cpy(g_lam0, g_lam_T, bNS);
+    cpy(g_M0, g_M_T, bNS);
+    if (e != cudaSuccess) return cuda_fail(e, "dg_backward");
+    return DG_OK;
+  }
+  char* w = (char*)workspace;
+  float* ck_lam = (float*)(w + L.ck_lam);
+  float* ck_M = (float*)(w + L.ck_M);
+  float* seg_lam = (float*)(w + L.seg_lam);
+  float* seg_S = (float*)(w + L.seg_S);
+  float* w_lam = (float*)(w + L.w_lam);
+  float* w_M = (float*)(w + L.w_M);
+  float* sdot = (float*)(w + L.sdot);
+  float* sd_next = (float*)(w + L.sd_a);
+  float* sd_cur = (float*)(w + L.sd_b);
+  const int threads = threads_of(opts);
+  SweepArgs fa{};
+  fa.lam = w_lam;
+  fa.M = w_M;
+  fa.omega = omega;
+  fa.alpha = alpha;
+  fa.omega0 = omega_of(opts);
+  fa.mode = mode;
+  // 1. forward pass keeping a checkpoint of (lambda, M) every k iterations
+  cpy(w_lam, lam0, bNS);
+  cpy(w_M, M0, bNS);
+  for (int c = 0; c < L.nseg; ++c) {
+    cpy(ck_lam + (size_t)c * NS, w_lam, bNS);
+    cpy(ck_M + (size_t)c * NS, w_M, bNS);
+    if (c + 1 == L.nseg) break;
+    for (int it = 0; it < L.k; ++it) {
+      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
+      launch_sweep(kFwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), st);
+      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
+      launch_sweep(kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), st);
+    }
+  }
+  // 2. segments newest first: recompute, keeping lambda and S at every sweep
+  //    start, then run the adjoint sweeps backwards
+  cpy(g_lam0, g_lam_T, bNS);
+  AdjArgs aa{};
+  aa.omega = omega;
+  aa.alpha = alpha;
+  aa.omega0 = omega_of(opts);
+  aa.mode = mode;
+  aa.g_lam = g_lam0;
+  aa.g_omega = g_omega;
+  aa.g_alpha = g_alpha;
+  aa.sdot = sdot;
+  const int last_sweep = 2 * iters - 1;
+  for (int c = L.nseg - 1; c >= 0; --c) {
+    const int it0 = c * L.k, it1 = std::min(iters, it0 + L.k);
+    const int nsw = 2 * (it1 - it0);
+    cpy(w_lam, ck_lam + (size_t)c * NS, bNS);
+    cpy(w_M, ck_M + (size_t)c * NS, bNS);
+    for (int sw = 0; sw < nsw; ++sw) {
+      cpy(seg_lam + (size_t)sw * NS, w_lam, bNS);
+      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
+      cpy(seg_S + (size_t)sw * n, A.S, bn);
+      if (sw + 1 < nsw) launch_sweep(sw % 2 == 0 ? kFwd : kBwd, A, fa, threads, ar->groups.data(),
+                                     (int)ar->groups.size(), st);
+    }
+    for (int sw = nsw - 1; sw >= 0; --sw) {
+      const int gsw = 2 * it0 + sw;
+      aa.lam_old = seg_lam + (size_t)sw * NS;
+      aa.S_in = seg_S + (size_t)sw * n;
+      aa.seed_M = gsw == last_sweep ? g_M_T : nullptr;
+      aa.sdot_next = gsw == last_sweep ? nullptr : sd_next;
+      launch_adjoint_sweep(sw % 2 == 0, A, aa, ar->adj_groups.data(), (int)ar->adj_groups.size(), ar->cta_smem_cap,
+                           st);
+      launch_reduce_slots(A, sdot, sd_cur, st);
+      std::swap(sd_next, sd_cur);
+    }
+  }
+  // 3. M0 only enters through the first snapshot S_i = sum_j M0_ij
+  launch_gather_var(A, sd_next, g_M0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_backward copies");
+  return check_launch("dg_backward");
 }
 
 }  // extern "C"

@@ -347,7 +347,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     }
     tile.maxw = maxw;
     smem_max = std::max(smem_max, sweep_smem_bytes(nmax, nh, 1));
-    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nmax, nh));
+    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nmax, nh, 1));
     P.max_tile_rows = std::max(P.max_tile_rows, nmax);
     P.max_tile_slots = std::max<int32_t>(P.max_tile_slots, (int32_t)tslots);
     P.max_tile_hops = std::max(P.max_tile_hops, nh);
@@ -372,6 +372,14 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
       gmax0 = std::max(gmax0, sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0));
     }
     if (T > 0) P.groups.push_back({t0, T, (int32_t)gmax, (int32_t)gmax0});
+  }
+  for (const LaunchGroup& g : P.groups) {
+    AdjGroup a{g.tile0, g.tile1, 0, 0};
+    for (int t = g.tile0; t < g.tile1; ++t) {
+      a.region0 = std::max<int32_t>(a.region0, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0));
+      a.region1 = std::max<int32_t>(a.region1, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1));
+    }
+    P.adj_groups.push_back(a);
   }
   const int64_t num_slots = slot_base;
   if (num_slots >= (int64_t)INT32_MAX || node_base >= (int64_t)INT32_MAX)

@@ -74,6 +74,13 @@ struct LaunchGroup {
   int32_t region_bytes0;  // without omega (mode 0)
 };
 
+// Tiles of one adjoint launch (the sweep's launch groups with the adjoint's
+// shared-memory footprint).
+struct AdjGroup {
+  int32_t tile0, tile1;
+  int32_t region0, region1;  // per-warp slice, mode 0 / mode 1
+};
+
 struct Plan {
   // sizes
   dg_sizes sizes{};
@@ -81,6 +88,7 @@ struct Plan {
   // host images of the device arrays
   std::vector<Tile> tiles;
   std::vector<LaunchGroup> groups;
+  std::vector<AdjGroup> adj_groups;
   std::vector<uint16_t> desc;
   std::vector<uint16_t> lohi8;
   std::vector<int32_t> slot_var, slot_row;
@@ -115,10 +123,13 @@ inline size_t sweep_smem_bytes(int nmax, int nhops, int mode) {
   size_t b = (size_t)nmax * kWarp * 8 + (size_t)(nmax - 2) * kWarp * 2 + (size_t)nhops * kWarp * (mode ? 18 : 10);
   return (b + 127) / 128 * 128;
 }
-// ... and in the adjoint kernels (adds per-node adjoints and per-slot
-// recomputed quantities).
-inline size_t adjoint_smem_bytes(int nmax, int nhops) {
-  size_t b = (size_t)nmax * kWarp * 16 + (size_t)nhops * kWarp * 32;
+// ... and in the adjoint kernels: two cost arrays (reused for their
+// gradients), an argmin record and the child codes per node; per slot the
+// descriptor, the argmin nodes of m0/m1, lambda, S, alpha, the lambda and M
+// gradients, m1 - m0, a gather buffer and (mode 1) omega.
+inline size_t adjoint_smem_bytes(int nmax, int nhops, int mode) {
+  const size_t nn = (size_t)nmax * kWarp, ns = (size_t)nhops * kWarp;
+  size_t b = nn * 10 + ns * (mode ? 36 : 32) + (size_t)(nmax - 2) * kWarp * 2;
   return (b + 127) / 128 * 128;
 }
 

@@ -36,6 +36,29 @@ void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st);
 void launch_lower_bound(const DevArena& A, double* lb_out, cudaStream_t st);
 void launch_seed_M(const DevArena& A, float* g_M, cudaStream_t st);
 
+// Backpropagation through one sweep (kernels_adjoint.cu).
+struct AdjArgs {
+  const float* lam_old;    // lambda at the start of the sweep (arena order)
+  const float* S_in;       // S at the start of the sweep (per variable)
+  const float* omega;      // mode 1
+  const float* alpha;      // mode 1
+  float omega0;            // mode 0
+  int mode;
+  const float* seed_M;     // nullable: gradient of the sweep's M output (per slot)
+  const float* sdot_next;  // nullable: S-dot of the next sweep (per variable)
+  float* g_lam;            // in: gradient of lambda after the sweep; out: before
+  float* g_omega;          // accumulated
+  float* g_alpha;          // accumulated
+  float* sdot;             // out: alpha * (gradient of lambda after the sweep), per slot
+};
+cudaError_t set_adjoint_smem_limit(size_t bytes);
+void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups,
+                          size_t cta_smem_cap, cudaStream_t st);
+// out_var[i] = sum over the slots q of variable i of x[q] (fixed order)
+void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cudaStream_t st);
+// out_slot[q] = v[variable of q] (0 for padding slots)
+void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st);
+
 // dg_lower_bound with its intermediates in a static device array (noalloc.cu).
 dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, int num_groups, int threads,
                               cudaStream_t st, const float* lam, const float* M, double* lb);

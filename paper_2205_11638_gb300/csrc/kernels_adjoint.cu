@@ -1,0 +1,420 @@
+// kernels_adjoint.cu -- backpropagation through one sweep of Alg. 1
+// (Alg. 2 "BlockUpdate backpropagation", Prop. 2, and the shortest-path
+// formulation of App. B: gradients of min-marginals flow along the argmin
+// arcs of the min-sum recursions).
+//
+// One warp per tile, one lane per BDD, as in the forward sweeps.  A lane
+// first recomputes its sweep exactly as k_sweep does (same FP32 operations,
+// so the same values) and records, per node, the argmin in-arc of SP(r, .)
+// (smallest (parent rank, beta) on ties) and the argmin out-arc of SP(., T)
+// (0-arc on ties), and per level the argmin nodes of m0 and m1 (smallest
+// rank on ties).  It then runs the reverse of the sweep level by level:
+//   lambda^new = lambda^old - M^new + alpha S^in,  M^new = omega (m1 - m0)
+// gives   S-dot contribution alpha * g, alpha-dot += g S^in,
+//         Mt = M-dot - g, omega-dot += Mt (m1 - m0),
+//         m1-dot = omega Mt, m0-dot = -omega Mt, lambda^old-dot = g + m1-dot
+// (g = gradient of lambda^new), and the min-marginal gradients are routed to
+// SP(r, .) and SP(., T) of the argmin nodes and from there, arc by arc, to the
+// lambdas on the argmin paths.  This equals Alg. 2's minimiser-vector formula
+// (the argmin paths are the minimisers s^j(i, beta)) at O(arcs) per sweep.
+#include "kernels.h"
+#include "sweep.cuh"
+
+namespace dg {
+
+namespace {
+
+// Shared-memory image of one tile in the adjoint kernels.
+struct AdjSmem {
+  float* a1;       // [32 * nmax] SP(., T), later its gradient
+  float* a2;       // [32 * nmax] SP(r, .), later its gradient
+  uint16_t* meta;  // [32 * nmax] parent node | beta << 8 | hi-choice << 9
+  uint16_t* code;  // [32 * (nmax - 2)]
+  uint16_t* desc;  // [32 * nh]
+  uint16_t* amin;  // [32 * nh] argmin node of m0 | argmin node of m1 << 8
+  float* lam;      // [32 * nh] lambda at sweep start
+  float* S;        // [32 * nh] S^in of the slot's variable
+  float* al;       // [32 * nh] alpha
+  float* om;       // [32 * nh] omega (mode 1)
+  float* gl;       // [32 * nh] lambda gradient (new -> old)
+  float* md;       // [32 * nh] gradient of M^new
+  float* diff;     // [32 * nh] m1 - m0
+  float* tmp;      // [32 * nh] variable ids, then gathered S-dot
+  int nmax, nh;
+};
+
+#define A1(n) s.a1[(n) * kWarp + lane]
+#define A2(n) s.a2[(n) * kWarp + lane]
+#define META(n) s.meta[(n) * kWarp + lane]
+
+template <int MODE>
+__device__ __forceinline__ AdjSmem carve_adj(unsigned char* p, const Tile& T) {
+  AdjSmem s;
+  s.nmax = T.nmax;
+  s.nh = T.nhops;
+  const int nn = s.nmax * kWarp, ns = s.nh * kWarp;
+  s.a1 = (float*)p;
+  p += (size_t)nn * 4;
+  s.a2 = (float*)p;
+  p += (size_t)nn * 4;
+  s.lam = (float*)p;
+  p += (size_t)ns * 4;
+  s.S = (float*)p;
+  p += (size_t)ns * 4;
+  s.al = (float*)p;
+  p += (size_t)ns * 4;
+  s.gl = (float*)p;
+  p += (size_t)ns * 4;
+  s.md = (float*)p;
+  p += (size_t)ns * 4;
+  s.diff = (float*)p;
+  p += (size_t)ns * 4;
+  s.tmp = (float*)p;
+  p += (size_t)ns * 4;
+  if (MODE == 1) {
+    s.om = (float*)p;
+    p += (size_t)ns * 4;
+  } else {
+    s.om = nullptr;
+  }
+  s.meta = (uint16_t*)p;
+  p += (size_t)nn * 2;
+  s.desc = (uint16_t*)p;
+  p += (size_t)ns * 2;
+  s.amin = (uint16_t*)p;
+  p += (size_t)ns * 2;
+  s.code = (uint16_t*)p;
+  return s;
+}
+
+}  // namespace
+
+template <int FWD, int MODE>
+__global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int region_bytes, int tile0, int tile1) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = tile0 + blockIdx.x * (blockDim.x >> 5) + warp;
+  if (tile >= tile1) return;
+  const Tile T = A.tiles[tile];
+  AdjSmem s = carve_adj<MODE>(smem + (size_t)warp * region_bytes, T);
+  const int ns = s.nh * kWarp;
+  const int64_t sb = T.slot_base;
+
+  // ---- staging ----------------------------------------------------------
+  copy_async(s.code, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+  copy_async(s.desc, A.desc + sb, ns * 2, lane);
+  copy_async(s.lam, a.lam_old + sb, ns * 4, lane);
+  copy_async(s.gl, a.g_lam + sb, ns * 4, lane);
+  copy_async(s.tmp, A.slot_var + sb, ns * 4, lane);
+  if (MODE == 1) {
+    copy_async(s.om, a.omega + sb, ns * 4, lane);
+    copy_async(s.al, a.alpha + sb, ns * 4, lane);
+  }
+  if (a.seed_M) copy_async(s.md, a.seed_M + sb, ns * 4, lane);
+  cp_async_commit();
+  A1(kTopCode) = 0.0f;
+  A1(kBotCode) = f_inf();
+  cp_async_wait_all();
+  __syncwarp();
+  {
+    int* sv = reinterpret_cast<int*>(s.tmp);
+    for (int q = lane; q < ns; q += kWarp) {
+      const int v = sv[q];
+      if (!a.seed_M) s.md[q] = 0.0f;
+      if (v >= 0) {
+        cp_async4(s.S + q, a.S_in + v);
+        if (MODE == 0) cp_async4(s.al + q, A.invdeg + v);
+        if (a.sdot_next)
+          cp_async4(s.tmp + q, a.sdot_next + v);
+        else
+          s.tmp[q] = 0.0f;
+      } else {
+        s.S[q] = 0.0f;
+        if (MODE == 0) s.al[q] = 0.0f;
+        s.tmp[q] = 0.0f;
+      }
+    }
+    cp_async_commit();
+  }
+
+  // ---- forward recompute with argmin records ----------------------------
+  if (FWD) {
+    // SP(., T) bottom-up under lambda^old; hi-choice bit per node
+    for (int h = s.nh - 1; h >= 0; --h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) continue;
+      const int fn = desc_first(ds);
+      const float l = s.lam[h * kWarp + lane];
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s.code, n, lane);
+        const float tl = A1(c & 0xFFu), th = l + A1(c >> 8);
+        const bool take0 = (c & 0xFFu) != kBotCode && tl <= th;
+        A1(n) = take0 ? tl : th;
+        META(n) = take0 ? 0 : (1u << 9);
+      }
+    }
+  } else {
+    // SP(r, .) top-down under lambda^old; argmin in-arc per node
+    if (desc_width(s.desc[lane]) > 0) A2(2) = 0.0f;
+    for (int h = 0; h + 1 < s.nh; ++h) {
+      const uint32_t ds = s.desc[h * kWarp + lane], dn = s.desc[(h + 1) * kWarp + lane];
+      const int w = desc_width(ds), wn = desc_width(dn);
+      if (wn == 0) break;
+      const int fn = desc_first(ds), fnn = desc_first(dn);
+      const float l = s.lam[h * kWarp + lane];
+      for (int r = 0; r < wn; ++r) A2(fnn + r) = f_inf();
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s.code, n, lane);
+        const uint32_t lo = c & 0xFFu, hi = c >> 8;
+        const float dv = A2(n);
+        if (lo >= 2 && dv < A2(lo)) {
+          A2(lo) = dv;
+          META(lo) = (uint16_t)n;
+        }
+        if (hi >= 2 && dv + l < A2(hi)) {
+          A2(hi) = dv + l;
+          META(hi) = (uint16_t)(n | (1u << 8));
+        }
+      }
+    }
+  }
+  wait_gathers();
+  for (int q = lane; q < ns; q += kWarp) s.md[q] += s.tmp[q];  // gradient of M^new
+  __syncwarp();
+
+  if (FWD) {
+    if (desc_width(s.desc[lane]) > 0) A2(2) = 0.0f;
+    for (int h = 0; h < s.nh; ++h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) break;
+      const int fn = desc_first(ds);
+      const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
+      const int wn = desc_width(dn), fnn = desc_first(dn);
+      float b0 = f_inf(), b1 = f_inf();
+      int v0 = fn, v1 = fn;
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s.code, n, lane);
+        const float dv = A2(n);
+        const float x0 = dv + A1(c & 0xFFu), x1 = dv + A1(c >> 8);
+        if (x0 < b0) { b0 = x0; v0 = n; }
+        if (x1 < b1) { b1 = x1; v1 = n; }
+      }
+      const int q = h * kWarp + lane;
+      const float l = s.lam[q];
+      const float m0 = b0, m1 = l + b1;
+      const float om = MODE == 1 ? s.om[q] : a.omega0;
+      const float Mn = om * (m1 - m0);
+      const float ln = l - Mn + s.al[q] * s.S[q];
+      s.diff[q] = m1 - m0;
+      s.amin[q] = (uint16_t)(v0 | (v1 << 8));
+      if (wn > 0) {
+        for (int r = 0; r < wn; ++r) A2(fnn + r) = f_inf();
+        for (int r = 0; r < w; ++r) {
+          const int n = fn + r;
+          const uint32_t c = node_code(s.code, n, lane);
+          const uint32_t lo = c & 0xFFu, hi = c >> 8;
+          const float dv = A2(n);
+          if (lo >= 2 && dv < A2(lo)) {
+            A2(lo) = dv;
+            META(lo) = (uint16_t)((META(lo) & (1u << 9)) | n);
+          }
+          if (hi >= 2 && dv + ln < A2(hi)) {
+            A2(hi) = dv + ln;
+            META(hi) = (uint16_t)((META(hi) & (1u << 9)) | n | (1u << 8));
+          }
+        }
+      }
+    }
+  } else {
+    for (int h = s.nh - 1; h >= 0; --h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) continue;
+      const int fn = desc_first(ds);
+      float b0 = f_inf(), b1 = f_inf();
+      int v0 = fn, v1 = fn;
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s.code, n, lane);
+        const float dv = A2(n);
+        const float x0 = dv + A1(c & 0xFFu), x1 = dv + A1(c >> 8);
+        if (x0 < b0) { b0 = x0; v0 = n; }
+        if (x1 < b1) { b1 = x1; v1 = n; }
+      }
+      const int q = h * kWarp + lane;
+      const float l = s.lam[q];
+      const float m0 = b0, m1 = l + b1;
+      const float om = MODE == 1 ? s.om[q] : a.omega0;
+      const float Mn = om * (m1 - m0);
+      const float ln = l - Mn + s.al[q] * s.S[q];
+      s.diff[q] = m1 - m0;
+      s.amin[q] = (uint16_t)(v0 | (v1 << 8));
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const uint32_t c = node_code(s.code, n, lane);
+        const float tl = A1(c & 0xFFu), th = ln + A1(c >> 8);
+        const bool take0 = (c & 0xFFu) != kBotCode && tl <= th;
+        A1(n) = take0 ? tl : th;
+        META(n) = (uint16_t)((META(n) & 0x1FFu) | (take0 ? 0u : (1u << 9)));
+      }
+    }
+  }
+
+  // ---- reverse ------------------------------------------------------------
+  for (int n = 0; n < s.nmax; ++n) {
+    A1(n) = 0.0f;  // gradient of SP(., T)
+    A2(n) = 0.0f;  // gradient of SP(r, .)
+  }
+  // one step of the reverse: the update and the min-marginal argmins of level h
+  auto reverse_level = [&](int h) {
+    const int q = h * kWarp + lane;
+    const float g = s.gl[q];
+    const float al = s.al[q];
+    const float om = MODE == 1 ? s.om[q] : a.omega0;
+    const float Mt = s.md[q] - g;
+    s.tmp[q] = al * g;                                       // contribution to S-dot
+    a.g_alpha[sb + q] += g * s.S[q];
+    a.g_omega[sb + q] += Mt * s.diff[q];
+    const float dm1 = om * Mt, dm0 = -om * Mt;
+    s.gl[q] = g + dm1;                                       // gradient of lambda^old
+    const uint32_t am = s.amin[q];
+    const int v0 = am & 0xFFu, v1 = am >> 8;
+    const uint32_t c0 = node_code(s.code, v0, lane), c1 = node_code(s.code, v1, lane);
+    A2(v0) += dm0;
+    A1(c0 & 0xFFu) += dm0;  // terminals absorb into their unused entries
+    A2(v1) += dm1;
+    A1(c1 >> 8) += dm1;
+  };
+  if (FWD) {
+    for (int h = s.nh - 1; h >= 0; --h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      if (desc_width(ds) == 0) continue;
+      const int q = h * kWarp + lane;
+      const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
+      const int wn = desc_width(dn), fnn = desc_first(dn);
+      // SP(r, .) of level h+1 was relaxed from level h with lambda^new_h
+      float g = s.gl[q];
+      for (int r = 0; r < wn; ++r) {
+        const int wnode = fnn + r;
+        const float gd = A2(wnode);
+        const uint32_t mt = META(wnode);
+        A2(mt & 0xFFu) += gd;
+        if (mt & (1u << 8)) g += gd;
+      }
+      s.gl[q] = g;
+      reverse_level(h);
+    }
+    // SP(., T) under lambda^old: route its gradient top-down along argmin out-arcs
+    for (int h = 0; h < s.nh; ++h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) break;
+      const int fn = desc_first(ds);
+      const int q = h * kWarp + lane;
+      float g = s.gl[q];
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const float gt = A1(n);
+        const uint32_t c = node_code(s.code, n, lane);
+        if (META(n) & (1u << 9)) {
+          A1(c >> 8) += gt;
+          g += gt;
+        } else {
+          A1(c & 0xFFu) += gt;
+        }
+      }
+      s.gl[q] = g;
+    }
+  } else {
+    for (int h = 0; h < s.nh; ++h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) break;
+      const int fn = desc_first(ds);
+      const int q = h * kWarp + lane;
+      // SP(., T) of level h was recomputed with lambda^new_h
+      float g = s.gl[q];
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const float gt = A1(n);
+        const uint32_t c = node_code(s.code, n, lane);
+        if (META(n) & (1u << 9)) {
+          A1(c >> 8) += gt;
+          g += gt;
+        } else {
+          A1(c & 0xFFu) += gt;
+        }
+      }
+      s.gl[q] = g;
+      reverse_level(h);
+    }
+    // SP(r, .) under lambda^old: route its gradient bottom-up along argmin in-arcs
+    for (int h = s.nh - 1; h >= 1; --h) {
+      const uint32_t ds = s.desc[h * kWarp + lane];
+      const int w = desc_width(ds);
+      if (w == 0) continue;
+      const int fn = desc_first(ds);
+      const int qp = (h - 1) * kWarp + lane;
+      float g = s.gl[qp];
+      for (int r = 0; r < w; ++r) {
+        const int n = fn + r;
+        const float gd = A2(n);
+        const uint32_t mt = META(n);
+        A2(mt & 0xFFu) += gd;
+        if (mt & (1u << 8)) g += gd;
+      }
+      s.gl[qp] = g;
+    }
+  }
+  __syncwarp();
+  // ---- outputs ----------------------------------------------------------
+  for (int q = lane; q < ns; q += kWarp) {
+    if (desc_width(s.desc[q]) == 0) continue;
+    a.g_lam[sb + q] = s.gl[q];
+    a.sdot[sb + q] = s.tmp[q];
+  }
+}
+
+template <int FWD>
+static cudaError_t set_adj_attr(int b) {
+  cudaError_t e = cudaFuncSetAttribute(k_adjoint<FWD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<FWD, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
+}
+
+cudaError_t set_adjoint_smem_limit(size_t bytes) {
+  cudaError_t e = set_adj_attr<1>((int)bytes);
+  if (e == cudaSuccess) e = set_adj_attr<0>((int)bytes);
+  return e;
+}
+
+template <int FWD, int MODE>
+static void launch_adj(const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups, size_t cap,
+                       cudaStream_t st) {
+  for (int g = 0; g < num_groups; ++g) {
+    const AdjGroup& G = groups[g];
+    const size_t region = (size_t)(MODE == 1 ? G.region1 : G.region0);
+    int wpc = 4;
+    while (wpc > 1 && region * wpc > cap) --wpc;
+    const int nt = G.tile1 - G.tile0;
+    k_adjoint<FWD, MODE><<<(nt + wpc - 1) / wpc, wpc * kWarp, region * wpc, st>>>(A, a, (int)region, G.tile0,
+                                                                                   G.tile1);
+  }
+}
+
+void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups,
+                          size_t cta_smem_cap, cudaStream_t st) {
+  if (forward)
+    a.mode == 1 ? launch_adj<1, 1>(A, a, groups, num_groups, cta_smem_cap, st)
+                : launch_adj<1, 0>(A, a, groups, num_groups, cta_smem_cap, st);
+  else
+    a.mode == 1 ? launch_adj<0, 1>(A, a, groups, num_groups, cta_smem_cap, st)
+                : launch_adj<0, 0>(A, a, groups, num_groups, cta_smem_cap, st);
+}
+
+}  // namespace dg

@@ -101,6 +101,34 @@ __global__ void k_seed_M(DevArena A, float* gM) {
   gM[q] = (var >= 0 && A.S[var] < 0.f) ? 1.f : 0.f;
 }
 
+__global__ void __launch_bounds__(256) k_reduce_slots(DevArena A, const float* __restrict__ x, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
+  float s = 0.f;
+  for (int k = b; k < e; ++k) s += x[__ldg(A.var_slots + k)];
+  out[i] = s;
+}
+
+__global__ void k_gather_var(DevArena A, const float* __restrict__ v, float* out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.num_slots) return;
+  const int var = __ldg(A.slot_var + q);
+  out[q] = var >= 0 ? v[var] : 0.f;
+}
+
+void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cudaStream_t st) {
+  const int T = 256;
+  const int G = (A.n + T - 1) / T;
+  if (G > 0) k_reduce_slots<<<G, T, 0, st>>>(A, x, out_var);
+}
+
+void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st) {
+  const int T = 256;
+  const int64_t G = (A.num_slots + T - 1) / T;
+  if (G > 0) k_gather_var<<<(unsigned)G, T, 0, st>>>(A, v, out_slot);
+}
+
 void launch_reduce_S(const DevArena& A, const float* M, float* lam, const float* alpha, int mode, bool renorm,
                      cudaStream_t st) {
   const int T = 256;

@@ -69,8 +69,11 @@ __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
 #define DG_D(s, n) (s).d[(n) * kWarp + lane]
 
 // Child codes (lo | hi << 8) of node number n >= 2 of my BDD.
+__device__ __forceinline__ uint32_t node_code(const uint16_t* code, int n, int lane) {
+  return code[(n - 2) * kWarp + lane];
+}
 __device__ __forceinline__ uint32_t node_code(const TileSmem& s, int n, int lane) {
-  return s.code[(n - 2) * kWarp + lane];
+  return node_code(s.code, n, lane);
 }
 
 // Asynchronous global -> shared copies (cp.async): 16 B for the streamed

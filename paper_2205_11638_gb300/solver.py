@@ -142,6 +142,18 @@ class Arena:
             _lib._lib.dg_destroy(self._h)
             self._h = None
 
+    def slot_instance(self):
+        """Instance of every arena slot (padding: 0), for per-instance scaling."""
+        if getattr(self, "_slot_inst", None) is None:
+            rp = self.plan._keep["row_ptr"]
+            irp = self.plan._keep.get("irp")
+            sm = self.plan.slot_to_csr
+            rows = np.searchsorted(rp, np.maximum(sm, 0), side="right") - 1
+            inst = np.zeros_like(rows) if irp is None else np.searchsorted(irp, rows, side="right") - 1
+            inst[sm < 0] = 0
+            self._slot_inst = torch.from_numpy(inst.astype(np.int64)).to(self.device)
+        return self._slot_inst
+
     # -- marshalling helpers (index permutations only) ---------------------
     def zeros(self, dtype=torch.float32):
         return torch.zeros(self.num_slots, dtype=dtype, device=self.device)
@@ -249,6 +261,57 @@ class Arena:
                                       *[_ptr(o) for o in outs], _ptr(workspace), int(workspace.numel()),
                                       ctypes.byref(self.options)), "dg_backward")
         return tuple(outs)
+
+
+class DualIterate(torch.autograd.Function):
+    """(lam0, M0, omega, alpha) -> (lam_T, M_T) through ``iters`` iterations of
+    Alg. 1 (dg_iterate); backward is Alg. 2 (dg_backward) with a checkpoint of
+    (lam, M) every ``ckpt_every`` iterations.  ``omega``/``alpha`` None selects
+    the plain method (scalar omega of the arena's options, alpha = 1/|J_i|)."""
+
+    @staticmethod
+    def forward(ctx, lam0, M0, omega, alpha, arena, iters, ckpt_every):
+        lam, M = lam0.detach().clone(), M0.detach().clone()
+        om = omega.detach() if omega is not None else None
+        al = alpha.detach() if alpha is not None else None
+        arena.iterate(lam, M, om, al, iters=iters)
+        ctx.arena, ctx.iters, ctx.ckpt = arena, int(iters), int(ckpt_every)
+        ctx.has_params = omega is not None
+        ctx.save_for_backward(lam0.detach(), M0.detach(), om, al)
+        return lam, M
+
+    @staticmethod
+    def backward(ctx, g_lam, g_M):
+        lam0, M0, om, al = ctx.saved_tensors
+        A = ctx.arena
+        g_lam = A.zeros() if g_lam is None else g_lam.contiguous().float()
+        g_M = A.zeros() if g_M is None else g_M.contiguous().float()
+        gl0, gM0, gw, ga = A.backward(lam0, M0, om, al, ctx.iters, ctx.ckpt, g_lam, g_M)
+        if not ctx.has_params:
+            gw = ga = None
+        return gl0, gM0, gw, ga, None, None, None
+
+
+class LowerBound(torch.autograd.Function):
+    """Per-instance lower bound (dg_lower_bound) with the loss gradient of
+    eq. (3) plus the unary term (dg_lb_seed) as backward."""
+
+    @staticmethod
+    def forward(ctx, lam, M, arena):
+        ctx.arena = arena
+        ctx.save_for_backward(lam.detach(), M.detach())
+        return arena.lower_bound(lam.detach(), M.detach())
+
+    @staticmethod
+    def backward(ctx, g):
+        lam, M = ctx.saved_tensors
+        A = ctx.arena
+        gl, gM = A.lb_seed(lam, M)
+        if A.num_inst == 1:
+            w = g.float()[0]
+            return gl * w, gM * w, None
+        scale = g.float()[A.slot_instance()]
+        return gl * scale, gM * scale, None
 
 
 class Graph:

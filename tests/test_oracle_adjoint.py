@@ -102,3 +102,37 @@ def test_gradient_of_M0_is_shared_per_variable():
         v = gM[P.col == i]
         if len(v):
             assert np.ptp(v) == 0.0
+
+
+@pytest.mark.parametrize("seed,iters", [(21, 1), (22, 2)])
+def test_oracle_backward_equals_dense_autograd(seed, iters):
+    """The oracle's Alg. 2 (minimiser vectors from its BDDs) against torch
+    autograd through a dense restatement of Alg. 1 (brute-force min-marginals):
+    two implementations with nothing in common."""
+    import torch
+
+    from tests import dense_ref
+
+    good = []
+    for r in workloads.random_rows(6 * 8, kmax=5, n=10, seed=seed):
+        try:
+            oracle.Oracle(workloads.single_rows_problem([r], 10, np.zeros(10)))
+            good.append(r)
+        except oracle.OracleError:
+            pass
+        if len(good) == 8:
+            break
+    rng = np.random.default_rng(seed)
+    prob = workloads.single_rows_problem(good, 10, rng.normal(size=10))
+    O = oracle.Oracle(prob)
+    lam, M, omega, alpha = _inputs(O, seed)
+    rng2 = np.random.default_rng(500 + seed)
+    a = rng2.normal(size=O.num_slots)
+    b = rng2.normal(size=O.num_slots)
+    gl, gM, gw, ga = O.backward(lam, M, omega, alpha, iters, a, b)
+    t = [torch.tensor(x, dtype=torch.float64, requires_grad=True) for x in (lam, M, omega, alpha)]
+    lT, MT = dense_ref.iterate(prob, *t, iters)
+    loss = (lT * torch.as_tensor(a)).sum() + (MT * torch.as_tensor(b)).sum()
+    loss.backward()
+    for mine, ref in zip((gl, gM, gw, ga), t):
+        np.testing.assert_allclose(mine, ref.grad.numpy(), atol=1e-9, rtol=1e-9)
