@@ -40,6 +40,7 @@ METRIC = "BDD-arc updates/s per dual iteration (forward+backward sweep)"
 UNIT = "arc-updates/s"
 WORKLOADS = {
     "tracking_500x2000": lambda: workloads.tracking(),
+    "tracking_200x2000": lambda: workloads.tracking(frames=200),
     "matching_quadratic_200": lambda: workloads.matching_quadratic(),
     "independent_set_10k": lambda: workloads.independent_set(),
 }
@@ -96,7 +97,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -185,6 +186,83 @@ def run_reference(args):
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def _batched_measurement(args, solver, torch, iters=50, ck=10):
+    """64 uneven instances (independent set, set cover, matching) in one arena,
+    ``iters`` iterations captured in one CUDA graph with per-instance FP64
+    bounds, against the same instances solved one arena per instance with
+    plain dg_iterate calls; then fwd + adjoint of the whole batch against
+    fwd + adjoint per instance."""
+    prob, kinds = workloads.batched_mix(num=64)
+    A = solver.plan(prob).bind()
+    stream = torch.cuda.Stream()
+    lam0, M0 = A.init_lambda()
+    lam, M = lam0.clone(), M0.clone()
+    lb = torch.zeros(A.num_inst, dtype=torch.float64, device=A.device)
+    with torch.cuda.stream(stream):
+        g = A.graph(lam, M, iters=iters, lb_out=lb, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        for r in range(reps + 1):
+            lam.copy_(lam0)
+            M.copy_(M0)
+            if r == 1:
+                e0.record(stream)
+            g.replay(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / reps
+    lb_batch = lb.cpu().numpy().copy()
+    # one arena per instance
+    irp, ivp = prob["inst_row_ptr"], prob["inst_var_ptr"]
+    singles = []
+    for k in range(len(irp) - 1):
+        r0, r1, v0, v1 = int(irp[k]), int(irp[k + 1]), int(ivp[k]), int(ivp[k + 1])
+        b0, b1 = int(prob["row_ptr"][r0]), int(prob["row_ptr"][r1])
+        sub = dict(n=v1 - v0, row_ptr=prob["row_ptr"][r0:r1 + 1] - b0, col=prob["col"][b0:b1] - v0,
+                   coef=prob["coef"][b0:b1], sense=prob["sense"][r0:r1], rhs=prob["rhs"][r0:r1], c=prob["c"][v0:v1])
+        singles.append(solver.plan(sub).bind())
+    states = [S.init_lambda() for S in singles]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lbs = []
+    for rep in range(2):
+        work = [(l.clone(), m.clone()) for (l, m) in states]
+        torch.cuda.synchronize()
+        e0.record()
+        lbs = [S.iterate(l, m, iters=iters, lb=True) for S, (l, m) in zip(singles, work)]
+        e1.record()
+        torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1)
+    lb_single = np.array([float(x[0]) for x in lbs])
+    rel = float(np.max(np.abs(lb_single - lb_batch) / np.maximum(1.0, np.abs(lb_single))))
+    # fwd + adjoint (lower-bound loss) on the batch vs per instance
+    def fwd_adj(S, l0, m0):
+        l, m = l0.clone(), m0.clone()
+        S.iterate(l, m, iters=iters)
+        gl, gM = S.lb_seed(l, m)
+        return S.backward(l0, m0, None, None, iters, ck, gl, gM)
+    fwd_adj(A, lam0, M0)
+    torch.cuda.synchronize()
+    e0.record()
+    fwd_adj(A, lam0, M0)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch_adj = e0.elapsed_time(e1)
+    e0.record()
+    for S, (l, m) in zip(singles, states):
+        fwd_adj(S, l, m)
+    e1.record()
+    torch.cuda.synchronize()
+    t_single_adj = e0.elapsed_time(e1)
+    return {"instances": int(A.num_inst), "kinds": {"independent_set": int((kinds == 0).sum()),
+            "set_cover": int((kinds == 1).sum()), "matching": int((kinds == 2).sum())},
+            "N_lambda": int(A.stats.sizes.num_lambda), "iterations": iters,
+            "batched_graph_ms": t_batch, "one_instance_per_launch_ms": t_single,
+            "speedup_plain": t_single / t_batch, "max_rel_bound_difference": rel,
+            "batched_fwd_adjoint_ms": t_batch_adj, "one_instance_per_launch_fwd_adjoint_ms": t_single_adj,
+            "speedup_fwd_adjoint": t_single_adj / t_batch_adj, "checkpoint_every": ck}
 
 
 def run_ours(args):
@@ -307,21 +385,58 @@ def run_ours(args):
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8 * A.num_inst,
                "ms_per_step": e_ms / ke, "steps": ke}
 
+    # fwd + adjoint of an unrolled solve (Alg. 1 forward, Alg. 2 backward with
+    # a checkpoint every 10 iterations) on the same instance
+    adjoint = None
+    if not args.no_adjoint:
+        T, ck = args.adjoint_iters, 10
+        lam0, M0 = A.init_lambda()
+        ws_bytes = A.backward_workspace_bytes(T, ck)
+        wsb = torch.empty(ws_bytes, dtype=torch.uint8, device=A.device)
+        gl = torch.empty_like(lam0)
+        gM = torch.empty_like(M0)
+        outs = [torch.empty_like(lam0) for _ in range(4)]
+        lamw, Mw = lam0.clone(), M0.clone()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for rep in range(2):  # first repetition warms up
+            lamw.copy_(lam0)
+            Mw.copy_(M0)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            A.iterate(lamw, Mw, iters=T)
+            A.lb_seed_into(lamw, Mw, gl, gM)
+            ev[1].record(stream)
+            A.backward_into(lam0, M0, None, None, T, ck, gl, gM, outs, wsb)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+        f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        adjoint = {"unrolled_iterations": T, "checkpoint_every": ck, "forward_ms": f_ms, "backward_ms": b_ms,
+                   "fwd_adjoint_ms_per_unrolled_step": (f_ms + b_ms) / T, "workspace_bytes": ws_bytes,
+                   "loss": "lower bound (eq. 3 plus unary term)"}
+        del wsb
+
+    batched = None
+    if not args.no_batched:
+        batched = _batched_measurement(args, solver, torch)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = _cpu_oracle_rate(args.cpu_budget)
 
-    launches_per_step = 6  # fwd sweep, S, bwd sweep, S, lb partial, lb final
+    # 2 sweeps x launch groups, 2 S reductions, lb partial, lb final
+    launches_per_step = 2 * int(st.sizes.num_launch_groups) + 4
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": args.workload, "n_vars": int(n), "constraints": int(st.sizes.m),
                       "N_lambda": int(Nl), "N_v": int(Nv), "arcs_per_iteration": int(arcs_per_iter),
-                      "tiles": int(st.sizes.num_tiles), "block_threads": args.threads or 256,
+                      "tiles": int(st.sizes.num_tiles), "launch_groups_per_sweep": int(st.sizes.num_launch_groups),
+                      "block_threads": args.threads or 128,
                       "l2": f"inputs larger than L2 (arena {st.sizes.arena_bytes / 1e6:.0f} MB + state "
                             f"{8 * A.num_slots / 1e6:.0f} MB)", "plan_bind_s": round(plan_s, 2),
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roof, "kernel_shares": shares, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+           "adjoint": adjoint, "batched": batched,
            "gpu_launches": launches_per_step * args.steps, "lower_bound_after_run": lb_final}
     if rank == 0:
         print(json.dumps(out))
@@ -342,6 +457,9 @@ def main():
     ap.add_argument("--tile-slots", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--adjoint-iters", type=int, default=100)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -27,6 +27,7 @@ using namespace dg;
 
 struct dg_arena_s {
   DevArena dev{};
+  StreamSet streams;  // auxiliary streams and events for concurrent launch groups
   std::vector<LaunchGroup> groups;
   std::vector<AdjGroup> adj_groups;
   size_t cta_smem_cap = 0;
@@ -50,6 +51,12 @@ int threads_of(const dg_options* o) {
   return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
 float omega_of(const dg_options* o) { return o && o->omega > 0.f ? o->omega : 0.5f; }
+
+StreamSet streams_for(const dg_arena* ar, cudaStream_t main) {
+  StreamSet s = ar->streams;
+  s.main = main;
+  return s;
+}
 
 dg_status check_launch(const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -75,10 +82,10 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   launch_reduce_S(A, M, lam, alpha, mode, false, st);
   for (int it = 0; it < iters; ++it) {
     a.E = nullptr;
-    launch_sweep(kFwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), st);
+    launch_sweep(kFwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     launch_reduce_S(A, M, lam, alpha, mode, false, st);
     if (lb_out && it == iters - 1) a.E = A.E;
-    launch_sweep(kBwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), st);
+    launch_sweep(kBwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
     launch_reduce_S(A, M, lam, alpha, mode, rn, st);
   }
@@ -87,7 +94,7 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
       SweepArgs e{};
       e.lam = lam;
       e.E = A.E;
-      launch_sweep(kEnergy, A, e, threads, ar->groups.data(), (int)ar->groups.size(), st);
+      launch_sweep(kEnergy, A, e, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     }
     launch_lower_bound(A, lb_out, st);
   }
@@ -235,6 +242,18 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   dg_arena* ar = new dg_arena();
   cudaGetDevice(&ar->device);
   {
+    bool ok = cudaEventCreateWithFlags(&ar->streams.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < kStreams - 1; ++k) {
+      ok = cudaStreamCreateWithFlags(&ar->streams.aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ar->streams.join[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      delete ar;
+      return fail(DG_ECUDA, "dg_bind: stream or event creation failed");
+    }
+    ar->streams.ready = true;
+  }
+  {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ar->device);
     ar->cta_smem_cap = (size_t)optin;
@@ -288,7 +307,17 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   return DG_OK;
 }
 
-void dg_destroy(dg_arena* arena) { delete arena; }
+void dg_destroy(dg_arena* arena) {
+  if (!arena) return;
+  if (arena->streams.ready) {
+    cudaEventDestroy(arena->streams.fork);
+    for (int k = 0; k < kStreams - 1; ++k) {
+      cudaStreamDestroy(arena->streams.aux[k]);
+      cudaEventDestroy(arena->streams.join[k]);
+    }
+  }
+  delete arena;
+}
 
 dg_status dg_get_stats(const dg_arena* arena, dg_stats* stats) {
   if (!arena || !stats) return fail(DG_EINVAL, "dg_get_stats: null argument");
@@ -349,7 +378,8 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
   a.omega0 = omega_of(opts);
   a.mode = mode;
   a.E = want_energy ? ar->dev.E : nullptr;
-  launch_sweep(forward ? kFwd : kBwd, ar->dev, a, threads_of(opts), ar->groups.data(), (int)ar->groups.size(), (cudaStream_t)stream);
+  launch_sweep(forward ? kFwd : kBwd, ar->dev, a, threads_of(opts), ar->groups.data(), (int)ar->groups.size(),
+               streams_for(ar, (cudaStream_t)stream));
   return check_launch("dg_sweep");
 }
 
@@ -368,7 +398,8 @@ dg_status dg_min_marginals(dg_arena* ar, void* stream, const float* lam, float* 
   a.lam = const_cast<float*>(lam);
   a.M = m0;
   a.out2 = m1;
-  launch_sweep(kMinMarg, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(), (cudaStream_t)stream);
+  launch_sweep(kMinMarg, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(),
+               streams_for(ar, (cudaStream_t)stream));
   return check_launch("dg_min_marginals");
 }
 
@@ -380,7 +411,8 @@ dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const flo
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
   a.E = ar->dev.E;
-  launch_sweep(kEnergy, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(), st);
+  launch_sweep(kEnergy, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(),
+               streams_for(ar, st));
   launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
   launch_lower_bound(ar->dev, lb, st);
   if (E_per_row) {
@@ -395,7 +427,7 @@ dg_status dg_lower_bound_noalloc(dg_arena* ar, void* stream, const float* lam, c
   if (!lam || !M || !lb) return fail(DG_EINVAL, "dg_lower_bound_noalloc: null pointer");
   if (dg_status s = check_vectors("dg_lower_bound_noalloc", lam, M)) return s;
   return lower_bound_noalloc(ar->dev, ar->groups.data(), (int)ar->groups.size(), threads_of(nullptr),
-                             (cudaStream_t)stream, lam, M, lb);
+                             streams_for(ar, (cudaStream_t)stream), lam, M, lb);
 }
 
 dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* M, float* g_lam, float* g_M) {
@@ -406,7 +438,8 @@ dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* 
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
   a.M = g_lam;
-  launch_sweep(kSeed, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(), st);
+  launch_sweep(kSeed, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(),
+               streams_for(ar, st));
   launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
   launch_seed_M(ar->dev, g_M, st);
   return check_launch("dg_lb_seed");
@@ -559,9 +592,9 @@ dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float
     if (c + 1 == L.nseg) break;
     for (int it = 0; it < L.k; ++it) {
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
-      launch_sweep(kFwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), st);
+      launch_sweep(kFwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
-      launch_sweep(kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), st);
+      launch_sweep(kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     }
   }
   // 2. segments newest first: recompute, keeping lambda and S at every sweep
@@ -586,8 +619,9 @@ dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float
       cpy(seg_lam + (size_t)sw * NS, w_lam, bNS);
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
       cpy(seg_S + (size_t)sw * n, A.S, bn);
-      if (sw + 1 < nsw) launch_sweep(sw % 2 == 0 ? kFwd : kBwd, A, fa, threads, ar->groups.data(),
-                                     (int)ar->groups.size(), st);
+      if (sw + 1 < nsw)
+        launch_sweep(sw % 2 == 0 ? kFwd : kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(),
+                     streams_for(ar, st));
     }
     for (int sw = nsw - 1; sw >= 0; --sw) {
       const int gsw = 2 * it0 + sw;
@@ -596,7 +630,7 @@ dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float
       aa.seed_M = gsw == last_sweep ? g_M_T : nullptr;
       aa.sdot_next = gsw == last_sweep ? nullptr : sd_next;
       launch_adjoint_sweep(sw % 2 == 0, A, aa, ar->adj_groups.data(), (int)ar->adj_groups.size(), ar->cta_smem_cap,
-                           st);
+                           streams_for(ar, st));
       launch_reduce_slots(A, sdot, sd_cur, st);
       std::swap(sd_next, sd_cur);
     }

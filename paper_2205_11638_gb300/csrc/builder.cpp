@@ -283,18 +283,18 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   // tile t takes BDDs order[32 t .. 32 t + 31]; tiles are then laid out by
   // shared-memory footprint, largest first, so that tiles of one launch group
   // are contiguous (and the longest tiles start first)
-  std::vector<int> tile_nh(T, 0), tile_nmax(T, 2), tile_order(T);
+  std::vector<int> tile_nh(T, 0), tile_nmax(T, 2), tile_maxw(T, 1), tile_order(T);
   for (int t = 0; t < T; ++t) {
     for (int64_t q = (int64_t)t * kWarp; q < std::min<int64_t>(m, (int64_t)(t + 1) * kWarp); ++q) {
       const int64_t j = order[q];
       tile_nh[t] = std::max<int>(tile_nh[t], (int)(R->row_ptr[j + 1] - R->row_ptr[j]));
       tile_nmax[t] = std::max<int>(tile_nmax[t], 2 + (int)(P.node_ptr[j + 1] - P.node_ptr[j]));
+      for (int64_t c = R->row_ptr[j]; c < R->row_ptr[j + 1]; ++c) tile_maxw[t] = std::max<int>(tile_maxw[t], width[c]);
     }
     tile_order[t] = t;
   }
-  std::stable_sort(tile_order.begin(), tile_order.end(), [&](int x, int y) {
-    return sweep_smem_bytes(tile_nmax[x], tile_nh[x], 1) > sweep_smem_bytes(tile_nmax[y], tile_nh[y], 1);
-  });
+  auto tile_smem = [&](int t) { return sweep_smem_bytes(tile_nmax[t], tile_nh[t], 1, ring_size(tile_maxw[t])); };
+  std::stable_sort(tile_order.begin(), tile_order.end(), [&](int x, int y) { return tile_smem(x) > tile_smem(y); });
   P.tiles.resize(T);
   P.slot_to_csr.clear();
   std::vector<int64_t> slot_of_csr(nnz, -1);
@@ -346,7 +346,8 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
       }
     }
     tile.maxw = maxw;
-    smem_max = std::max(smem_max, sweep_smem_bytes(nmax, nh, 1));
+    tile.ring = ring_size(maxw);
+    smem_max = std::max(smem_max, sweep_smem_bytes(nmax, nh, 1, tile.ring));
     smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nmax, nh, 1));
     P.max_tile_rows = std::max(P.max_tile_rows, nmax);
     P.max_tile_slots = std::max<int32_t>(P.max_tile_slots, (int32_t)tslots);
@@ -361,20 +362,41 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     int32_t t0 = 0;
     size_t gmax = 0, gmax0 = 0;
     for (int t = 0; t < T; ++t) {
-      const size_t r = sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1);
+      const size_t r = sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1, P.tiles[t].ring);
       if (t > t0 && (double)r < kGroupRatio * (double)gmax) {
-        P.groups.push_back({t0, t, (int32_t)gmax, (int32_t)gmax0});
+        P.groups.push_back({t0, t, (int32_t)gmax, (int32_t)gmax0, 0, 0, 0, 0, 0});
         t0 = t;
         gmax = 0;
         gmax0 = 0;
       }
       gmax = std::max(gmax, r);
-      gmax0 = std::max(gmax0, sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0));
+      gmax0 = std::max(gmax0, sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0, P.tiles[t].ring));
     }
-    if (T > 0) P.groups.push_back({t0, T, (int32_t)gmax, (int32_t)gmax0});
+    if (T > 0) P.groups.push_back({t0, T, (int32_t)gmax, (int32_t)gmax0, 0, 0, 0, 0, 0});
+    for (LaunchGroup& g : P.groups)
+      for (int t = g.tile0; t < g.tile1; ++t) {
+        g.region_bwd1 = std::max<int32_t>(g.region_bwd1, (int32_t)sweep_smem_bytes_bwd(P.tiles[t].nmax, P.tiles[t].nhops, 1));
+        g.region_bwd0 = std::max<int32_t>(g.region_bwd0, (int32_t)sweep_smem_bytes_bwd(P.tiles[t].nmax, P.tiles[t].nhops, 0));
+        smem_max = std::max<size_t>(smem_max, (size_t)g.region_bwd1);
+      }
+    // work estimate per group, then longest-processing-time assignment of the
+    // groups to the kStreams streams that run one sweep's launches concurrently
+    for (LaunchGroup& g : P.groups)
+      for (int t = g.tile0; t < g.tile1; ++t) g.work += (int64_t)kWarp * P.tiles[t].nmax * P.tiles[t].nhops;
+    std::vector<int> idx(P.groups.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return P.groups[x].work > P.groups[y].work; });
+    std::vector<int64_t> load(kStreams, 0);
+    for (int gi : idx) {
+      int best = 0;
+      for (int k = 1; k < kStreams; ++k)
+        if (load[k] < load[best]) best = k;
+      P.groups[gi].stream = best;
+      load[best] += P.groups[gi].work;
+    }
   }
   for (const LaunchGroup& g : P.groups) {
-    AdjGroup a{g.tile0, g.tile1, 0, 0};
+    AdjGroup a{g.tile0, g.tile1, 0, 0, g.stream, 0};
     for (int t = g.tile0; t < g.tile1; ++t) {
       a.region0 = std::max<int32_t>(a.region0, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0));
       a.region1 = std::max<int32_t>(a.region1, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1));

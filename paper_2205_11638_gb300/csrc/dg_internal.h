@@ -21,6 +21,7 @@ constexpr uint32_t kBotCode = 1u;
 constexpr int kMaxNodesPerBdd = 254;
 constexpr int kWarp = 32;
 constexpr int kMaxWidth = 32;  // nodes of one BDD level
+constexpr int kStreams = 4;    // streams one sweep's launch groups run on
 
 // One tile = up to 32 BDDs swept by one warp, BDD b by lane b.  Per-tile
 // arrays are interleaved by lane: slot (h, b) is slot_base + 32 h + b (its
@@ -34,9 +35,16 @@ struct Tile {
   int32_t nhops;      // longest BDD of the tile
   int32_t nbdd;       // BDDs (lanes in use)
   int32_t maxw;       // widest level
-  int32_t pad0, pad1;
+  int32_t ring;       // ring size (power of two >= 2 * maxw) of the sweep-direction costs
+  int32_t pad1;
 };
 static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
+
+inline int ring_size(int maxw) {
+  int r = 2;
+  while (r < 2 * maxw) r <<= 1;
+  return r;
+}
 
 // Device view of an arena (all pointers inside the caller's buffer).
 struct DevArena {
@@ -72,6 +80,11 @@ struct LaunchGroup {
   int32_t tile0, tile1;
   int32_t region_bytes;   // per-slot omega staged (mode 1)
   int32_t region_bytes0;  // without omega (mode 0)
+  int32_t region_bwd1;    // backward sweeps (two full cost arrays), mode 1
+  int32_t region_bwd0;    // ... mode 0
+  int64_t work;           // estimated cost: sum over tiles of 32 * nmax * nhops
+  int32_t stream;         // stream of the fork/join set the group runs on
+  int32_t pad;
 };
 
 // Tiles of one adjoint launch (the sweep's launch groups with the adjoint's
@@ -79,6 +92,8 @@ struct LaunchGroup {
 struct AdjGroup {
   int32_t tile0, tile1;
   int32_t region0, region1;  // per-warp slice, mode 0 / mode 1
+  int32_t stream;
+  int32_t pad;
 };
 
 struct Plan {
@@ -116,12 +131,19 @@ struct Plan {
 };
 
 // Shared-memory footprint of one tile (one warp's slice) in the sweep
-// kernels: two cost arrays of 32 x nmax floats and the child codes of
-// 32 x (nmax - 2) nodes, and per slot its descriptor, lambda, the gathered
-// S term and (mode 1) omega and alpha.
-inline size_t sweep_smem_bytes(int nmax, int nhops, int mode) {
-  size_t b = (size_t)nmax * kWarp * 8 + (size_t)(nmax - 2) * kWarp * 2 + (size_t)nhops * kWarp * (mode ? 18 : 10);
+// kernels: the costs of the first pass (32 x nmax floats), a ring of two
+// levels for the costs of the sweep direction (32 x ring floats), the child
+// codes of 32 x (nmax - 2) nodes, and per slot its descriptor, lambda, the
+// gathered S term and (mode 1) omega and alpha.
+inline size_t sweep_smem_bytes(int nmax, int nhops, int mode, int ring) {
+  size_t b = (size_t)nmax * kWarp * 4 + (size_t)ring * kWarp * 4 + (size_t)(nmax - 2) * kWarp * 2 +
+             (size_t)nhops * kWarp * (mode ? 18 : 10);
   return (b + 127) / 128 * 128;
+}
+// The backward sweeps keep both cost arrays whole (the ring would need a
+// test for terminal children on every arc): as above with ring = nmax.
+inline size_t sweep_smem_bytes_bwd(int nmax, int nhops, int mode) {
+  return sweep_smem_bytes(nmax, nhops, mode, nmax);
 }
 // ... and in the adjoint kernels: two cost arrays (reused for their
 // gradients), an argmin record and the child codes per node; per slot the

@@ -20,12 +20,27 @@ struct SweepArgs {
   float* E;            // nullable: E^j per original row (kBwd, kEnergy)
 };
 
+// The caller's stream plus kStreams - 1 auxiliary streams of an arena: the
+// launch groups of one sweep fork from the caller's stream, run on their
+// assigned streams concurrently, and join back before the next step.
+struct StreamSet {
+  cudaStream_t main = nullptr;
+  cudaStream_t aux[kStreams - 1] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kStreams - 1] = {};
+  bool ready = false;
+  cudaStream_t of(int k) const { return k == 0 || !ready ? main : aux[k - 1]; }
+  void begin() const;  // fork
+  void end() const;    // join
+};
+
 cudaError_t set_sweep_smem_limit(size_t bytes);
 // Dynamic shared memory one CTA may use; launchers put fewer warps in a CTA
 // when their tiles need more.
 void set_cta_smem_cap(size_t bytes);
+int best_warps_per_cta(size_t region, int max_wpc, size_t cta_cap);
 void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
-                  int num_groups, cudaStream_t st);
+                  int num_groups, const StreamSet& ss);
 
 // S_i = sum_{k in J_i} M_ik in fixed slot order; with renorm, also
 // lambda_ij += alpha_ij * (c_i - sum_k (lambda_ik + M_ik)) computed in FP64.
@@ -53,7 +68,7 @@ struct AdjArgs {
 };
 cudaError_t set_adjoint_smem_limit(size_t bytes);
 void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups,
-                          size_t cta_smem_cap, cudaStream_t st);
+                          size_t cta_smem_cap, const StreamSet& ss);
 // out_var[i] = sum over the slots q of variable i of x[q] (fixed order)
 void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cudaStream_t st);
 // out_slot[q] = v[variable of q] (0 for padding slots)
@@ -61,6 +76,6 @@ void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaS
 
 // dg_lower_bound with its intermediates in a static device array (noalloc.cu).
 dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, int num_groups, int threads,
-                              cudaStream_t st, const float* lam, const float* M, double* lb);
+                              const StreamSet& ss, const float* lam, const float* M, double* lb);
 
 }  // namespace dg

@@ -395,20 +395,22 @@ cudaError_t set_adjoint_smem_limit(size_t bytes) {
 
 template <int FWD, int MODE>
 static void launch_adj(const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups, size_t cap,
-                       cudaStream_t st) {
+                       const StreamSet& ss) {
+  const bool fork = num_groups > 1;
+  if (fork) ss.begin();
   for (int g = 0; g < num_groups; ++g) {
     const AdjGroup& G = groups[g];
     const size_t region = (size_t)(MODE == 1 ? G.region1 : G.region0);
-    int wpc = 4;
-    while (wpc > 1 && region * wpc > cap) --wpc;
+    const int wpc = best_warps_per_cta(region, 4, cap);
     const int nt = G.tile1 - G.tile0;
-    k_adjoint<FWD, MODE><<<(nt + wpc - 1) / wpc, wpc * kWarp, region * wpc, st>>>(A, a, (int)region, G.tile0,
-                                                                                   G.tile1);
+    k_adjoint<FWD, MODE><<<(nt + wpc - 1) / wpc, wpc * kWarp, region * wpc, fork ? ss.of(G.stream) : ss.main>>>(
+        A, a, (int)region, G.tile0, G.tile1);
   }
+  if (fork) ss.end();
 }
 
 void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups,
-                          size_t cta_smem_cap, cudaStream_t st) {
+                          size_t cta_smem_cap, const StreamSet& st) {
   if (forward)
     a.mode == 1 ? launch_adj<1, 1>(A, a, groups, num_groups, cta_smem_cap, st)
                 : launch_adj<1, 0>(A, a, groups, num_groups, cta_smem_cap, st);

@@ -51,19 +51,34 @@ __global__ void k_init(DevArena A, float* lam, float* M) {
   M[q] = 0.f;
 }
 
-// One FP64 partial sum per chunk: rows contribute E^j, variables
-// min(0, S_i) (or min(0, c_i) when no row covers them).
+// One partial sum per chunk: rows contribute E^j, variables min(0, S_i)
+// (or min(0, c_i) when no row covers them).  FP64 arithmetic is slow on this
+// part, so every thread accumulates its float32 terms with Knuth's TwoSum
+// (an error-free transformation: the running sum and its exact rounding
+// error, both float32), and only the per-thread results are combined in
+// FP64, in a fixed order (deterministic for a given layout).
 __global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
   const int4 ch = __ldg(A.lb_chunks + blockIdx.x);
-  double acc = 0.0;
+  float hi = 0.f, lo = 0.f;
+  double unc = 0.0;  // uncovered variables: float64 costs
   for (int x = ch.z + threadIdx.x; x < ch.w; x += blockDim.x) {
+    float v;
     if (ch.y == 0) {
-      acc += (double)A.E[x];
+      v = A.E[x];
     } else {
       const int deg = __ldg(A.var_ptr + x + 1) - __ldg(A.var_ptr + x);
-      acc += deg > 0 ? fmin(0.0, (double)A.S[x]) : fmin(0.0, A.c[x]);
+      if (deg == 0) {
+        unc += fmin(0.0, A.c[x]);
+        continue;
+      }
+      v = fminf(0.f, A.S[x]);
     }
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
   }
+  double acc = (double)hi + (double)lo + unc;
   __shared__ double red[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);

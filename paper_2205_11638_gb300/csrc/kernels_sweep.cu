@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
   const int tile = tile0 + blockIdx.x * (blockDim.x >> 5) + warp;
   if (tile >= tile1) return;  // whole warp leaves; no CTA-wide barrier follows
   const Tile T = A.tiles[tile];
-  TileSmem s = carve<MODE>(smem + (size_t)warp * region_bytes, T);
+  TileSmem s = carve<MODE, KIND != kBwd>(smem + (size_t)warp * region_bytes, T);
   load_tile<KIND == kFwd || KIND == kBwd, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane);
   const int64_t sbase = T.slot_base;
 
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
     // ---- SP(., T) under lambda at sweep start, then the forward sweep -----
     lane_cost_to_top(s, lane);
     if (KIND == kFwd) wait_gathers();
-    if (desc_width(s.desc[lane]) > 0) DG_D(s, 2) = 0.0f;
+    if (desc_width(s.desc[lane]) > 0) DG_R(s, 2) = 0.0f;
     for (int h = 0; h < s.nh; ++h) {
       const uint32_t ds = s.desc[h * kWarp + lane];
       const int w = desc_width(ds);
@@ -45,9 +45,9 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
-        const float dv = DG_D(s, n);
-        b0 = fminf(b0, dv + DG_T(s, c & 0xFFu));
-        b1 = fminf(b1, dv + DG_T(s, c >> 8));
+        const float dv = DG_R(s, n);
+        b0 = fminf(b0, dv + DG_F(s, c & 0xFFu));
+        b1 = fminf(b1, dv + DG_F(s, c >> 8));
       }
       const int q = h * kWarp + lane;
       const float l = s.lam[q];
@@ -64,14 +64,14 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         a.M[sbase + q] = Mn;
       }
       if (wn > 0) {
-        for (int r = 0; r < wn; ++r) DG_D(s, fnn + r) = f_inf();
+        for (int r = 0; r < wn; ++r) DG_R(s, fnn + r) = f_inf();
         for (int r = 0; r < w; ++r) {
           const int n = fn + r;
           const uint32_t c = node_code(s, n, lane);
           const uint32_t lo = c & 0xFFu, hi = c >> 8;
-          const float dv = DG_D(s, n);
-          DG_D(s, lo) = fminf(DG_D(s, lo), dv);  // bottom's d entry is scratch
-          DG_D(s, hi) = fminf(DG_D(s, hi), dv + ln);
+          const float dv = DG_R(s, n);
+          if (lo != kBotCode) DG_R(s, lo) = fminf(DG_R(s, lo), dv);
+          if (hi != kBotCode) DG_R(s, hi) = fminf(DG_R(s, hi), dv + ln);
         }
       }
     }
@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
     // ---- SP(r, .) under lambda at sweep start, then the backward sweep ----
     lane_cost_from_root(s, lane);
     wait_gathers();
+    DG_W(s, kTopCode) = 0.0f;
+    DG_W(s, kBotCode) = f_inf();
     for (int h = s.nh - 1; h >= 0; --h) {
       const uint32_t ds = s.desc[h * kWarp + lane];
       const int w = desc_width(ds);
@@ -88,9 +90,9 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
-        const float dv = DG_D(s, n);
-        b0 = fminf(b0, dv + DG_T(s, c & 0xFFu));
-        b1 = fminf(b1, dv + DG_T(s, c >> 8));
+        const float dv = DG_F(s, n);
+        b0 = fminf(b0, dv + DG_W(s, c & 0xFFu));
+        b1 = fminf(b1, dv + DG_W(s, c >> 8));
       }
       const int q = h * kWarp + lane;
       const float l = s.lam[q];
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
-        DG_T(s, n) = fminf(DG_T(s, c & 0xFFu), ln + DG_T(s, c >> 8));
+        DG_W(s, n) = fminf(DG_W(s, c & 0xFFu), ln + DG_W(s, c >> 8));
       }
     }
   } else {
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const uint32_t c = node_code(s, n, lane);
       const uint32_t lo = c & 0xFFu, hi = c >> 8;
       const int q = h * kWarp + lane;
-      const bool take0 = lo != kBotCode && (hi == kBotCode || DG_T(s, lo) <= s.lam[q] + DG_T(s, hi));
+      const bool take0 = lo != kBotCode && (hi == kBotCode || DG_F(s, lo) <= s.lam[q] + DG_F(s, hi));
       a.M[sbase + q] = take0 ? 0.f : 1.f;
       n = (int)(take0 ? lo : hi);
     }
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
   if ((KIND == kBwd || KIND == kEnergy) && a.E != nullptr && lane < T.nbdd) {
     // SP(root, T) = E^j of my BDD
     const int row = __ldg(A.slot_row + sbase + lane);
-    a.E[row] = DG_T(s, 2);
+    a.E[row] = KIND == kBwd ? DG_W(s, 2) : DG_F(s, 2);
   }
 }
 
@@ -152,26 +154,66 @@ cudaError_t set_sweep_smem_limit(size_t bytes) {
 static size_t g_cta_smem_cap = 227 * 1024;
 void set_cta_smem_cap(size_t bytes) { g_cta_smem_cap = bytes; }
 
+// Warps per CTA for a per-warp slice of `region` bytes: the CTA size (1, 2
+// or 4 warps, at most `max_wpc`) that lets the most warps share one SM (228 KB
+// of shared memory, 1 KB reserved per CTA, at most 32 CTAs and 64 warps).
+int best_warps_per_cta(size_t region, int max_wpc, size_t cta_cap) {
+  const size_t sm_smem = 228 * 1024;
+  int best = 1, best_warps = -1;
+  for (int w = 1; w <= max_wpc; w *= 2) {
+    const size_t cta = region * w;
+    if (cta > cta_cap) break;
+    int ctas = (int)(sm_smem / (cta + 1024));
+    if (ctas > 32) ctas = 32;
+    int warps = ctas * w;
+    if (warps > 64) warps = 64;
+    if (warps >= best_warps) {
+      best_warps = warps;
+      best = w;
+    }
+  }
+  return best;
+}
+
+void StreamSet::begin() const {
+  if (!ready) return;
+  cudaEventRecord(fork, main);
+  for (int k = 0; k < kStreams - 1; ++k) cudaStreamWaitEvent(aux[k], fork, 0);
+}
+
+void StreamSet::end() const {
+  if (!ready) return;
+  for (int k = 0; k < kStreams - 1; ++k) {
+    cudaEventRecord(join[k], aux[k]);
+    cudaStreamWaitEvent(main, join[k], 0);
+  }
+}
+
 template <int KIND, int MODE>
 static void launch_groups(const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
-                          int num_groups, cudaStream_t st) {
+                          int num_groups, const StreamSet& ss) {
+  const bool fork = num_groups > 1;
+  if (fork) ss.begin();
   for (int g = 0; g < num_groups; ++g) {
     const LaunchGroup& G = groups[g];
-    const size_t region = (size_t)(MODE == 1 ? G.region_bytes : G.region_bytes0);
+    const size_t region = (size_t)(KIND == kBwd ? (MODE == 1 ? G.region_bwd1 : G.region_bwd0)
+                                                : (MODE == 1 ? G.region_bytes : G.region_bytes0));
     int wpc = threads / kWarp;
     if (wpc > 4) wpc = 4;  // __launch_bounds__(128)
-    while (wpc > 1 && region * wpc > g_cta_smem_cap) --wpc;
+    wpc = best_warps_per_cta(region, wpc, g_cta_smem_cap);
     const int nt = G.tile1 - G.tile0;
     dim3 grid((nt + wpc - 1) / wpc), block(wpc * kWarp);
-    k_sweep<KIND, MODE><<<grid, block, region * wpc, st>>>(A, a, (int)region, G.tile0, G.tile1);
+    k_sweep<KIND, MODE><<<grid, block, region * wpc, fork ? ss.of(G.stream) : ss.main>>>(A, a, (int)region, G.tile0,
+                                                                                          G.tile1);
   }
+  if (fork) ss.end();
 }
 
 // One launch per launch group; threads = warps per CTA * 32, every warp
 // sweeps one tile with its own slice of the group's shared memory.  Only
 // the update sweeps read omega/alpha, so only they have a mode-1 variant.
 void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
-                  int num_groups, cudaStream_t st) {
+                  int num_groups, const StreamSet& st) {
   const bool m1 = a.mode == 1;
   switch (kind) {
     case kFwd:

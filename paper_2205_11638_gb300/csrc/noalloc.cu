@@ -62,7 +62,8 @@ size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, int num_groups, int threads,
-                              cudaStream_t st, const float* lam, const float* M, double* lb) {
+                              const StreamSet& ss, const float* lam, const float* M, double* lb) {
+  cudaStream_t st = ss.main;
   const size_t bE = up256((size_t)arena.m * 4), bS = up256((size_t)arena.n * 4);
   const size_t bP = up256((size_t)arena.num_lb_chunks * 8);
   const size_t need = bE + 2 * bS + bP;
@@ -81,7 +82,7 @@ dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, 
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
   a.E = A.E;
-  launch_sweep(kEnergy, A, a, threads, groups, num_groups, st);
+  launch_sweep(kEnergy, A, a, threads, groups, num_groups, ss);
   launch_reduce_S(A, M, nullptr, nullptr, 0, false, st);
   launch_lower_bound(A, lb, st);
   cudaError_t e = cudaGetLastError();

@@ -25,27 +25,30 @@ __device__ __forceinline__ int desc_first(uint32_t ds) { return (int)(ds & 0xFFu
 
 // Shared-memory image of one tile (one warp's slice).
 struct TileSmem {
-  float* t;        // [32 * nmax] SP(v, top), lane-interleaved
-  float* d;        // [32 * nmax] SP(root, v), lane-interleaved
+  float* full;     // [32 * nmax] costs of the first pass (all levels), lane-interleaved
+  float* ring;     // [32 * ring] costs of the sweep direction, two levels live
   float* lam;      // [32 * nh]
   float* sg;       // [32 * nh] variable of the slot, then the gathered S term
   float* om;       // [32 * nh] omega_ij (mode 1)
   float* al;       // [32 * nh] alpha_ij (mode 1)
   uint16_t* desc;  // [32 * nh]
   uint16_t* code;  // [32 * (nmax - 2)] child codes (lo | hi << 8), lane-interleaved
-  int nmax, nh;
+  int nmax, nh, rmask;
 };
 
-template <int MODE>
+// RING: the sweep-direction costs live in a ring of T.ring node numbers;
+// otherwise in a second whole array (s.ring then indexed by node number).
+template <int MODE, bool RING>
 __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
   TileSmem s;
   s.nmax = T.nmax;
   s.nh = T.nhops;
   const int ns = s.nh * kWarp;
-  s.t = (float*)p;
+  s.rmask = T.ring - 1;
+  s.full = (float*)p;
   p += (size_t)s.nmax * kWarp * 4;
-  s.d = (float*)p;
-  p += (size_t)s.nmax * kWarp * 4;
+  s.ring = (float*)p;
+  p += (size_t)(RING ? T.ring : s.nmax) * kWarp * 4;
   s.lam = (float*)p;
   p += (size_t)ns * 4;
   s.sg = (float*)p;
@@ -64,9 +67,14 @@ __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
   return s;
 }
 
-// Cost arrays of lane `lane`: element of node number n.
-#define DG_T(s, n) (s).t[(n) * kWarp + lane]
-#define DG_D(s, n) (s).d[(n) * kWarp + lane]
+// Cost arrays of lane `lane`: DG_F is the element of node number n in the
+// first-pass array (numbers 0 and 1 hold the terminal costs 0 and +inf);
+// DG_R the ring element of node number n >= 2 (the two live levels always
+// occupy fewer than `ring` consecutive node numbers).
+#define DG_F(s, n) (s).full[(n) * kWarp + lane]
+#define DG_R(s, n) (s).ring[((((int)(n)) - 2) & (s).rmask) * kWarp + lane]
+// second whole array (backward sweeps): element of node number n
+#define DG_W(s, n) (s).ring[(n) * kWarp + lane]
 
 // Child codes (lo | hi << 8) of node number n >= 2 of my BDD.
 __device__ __forceinline__ uint32_t node_code(const uint16_t* code, int n, int lane) {
@@ -115,8 +123,8 @@ __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, Tile
     }
   }
   cp_async_commit();
-  DG_T(s, kTopCode) = 0.0f;
-  DG_T(s, kBotCode) = f_inf();
+  DG_F(s, kTopCode) = 0.0f;
+  DG_F(s, kBotCode) = f_inf();
   cp_async_wait_all();
   __syncwarp();
   if (WITH_S) {
@@ -146,7 +154,8 @@ __device__ __forceinline__ float slot_avg(const TileSmem& s, int q) {
   return MODE == 1 ? s.al[q] * s.sg[q] : s.sg[q];
 }
 
-// SP(v, top) of every node of my BDD under s.lam (levels bottom-up).
+// SP(v, top) of every node of my BDD under s.lam into s.full (levels
+// bottom-up).
 __device__ __forceinline__ void lane_cost_to_top(TileSmem& s, int lane) {
   for (int h = s.nh - 1; h >= 0; --h) {
     const uint32_t ds = s.desc[h * kWarp + lane];
@@ -157,15 +166,16 @@ __device__ __forceinline__ void lane_cost_to_top(TileSmem& s, int lane) {
     for (int r = 0; r < w; ++r) {
       const int n = fn + r;
       const uint32_t c = node_code(s, n, lane);
-      DG_T(s, n) = fminf(DG_T(s, c & 0xFFu), l + DG_T(s, c >> 8));
+      DG_F(s, n) = fminf(DG_F(s, c & 0xFFu), l + DG_F(s, c >> 8));
     }
   }
 }
 
-// SP(root, v) of every node of my BDD under s.lam (levels top-down).
+// SP(root, v) of every node of my BDD under s.lam into s.full (levels
+// top-down).
 __device__ __forceinline__ void lane_cost_from_root(TileSmem& s, int lane) {
   if (desc_width(s.desc[lane]) == 0) return;
-  DG_D(s, 2) = 0.0f;
+  DG_F(s, 2) = 0.0f;
   for (int h = 0; h + 1 < s.nh; ++h) {
     const uint32_t ds = s.desc[h * kWarp + lane];
     const uint32_t dn = s.desc[(h + 1) * kWarp + lane];
@@ -173,15 +183,15 @@ __device__ __forceinline__ void lane_cost_from_root(TileSmem& s, int lane) {
     if (wn == 0) break;
     const int fn = desc_first(ds), fnn = desc_first(dn);
     const float l = s.lam[h * kWarp + lane];
-    for (int r = 0; r < wn; ++r) DG_D(s, fnn + r) = f_inf();
+    for (int r = 0; r < wn; ++r) DG_F(s, fnn + r) = f_inf();
     for (int r = 0; r < w; ++r) {
       const int n = fn + r;
       const uint32_t c = node_code(s, n, lane);
       const uint32_t lo = c & 0xFFu, hi = c >> 8;
-      const float dv = DG_D(s, n);
-      // arcs into the bottom terminal write its unused d entry
-      DG_D(s, lo) = fminf(DG_D(s, lo), dv);
-      DG_D(s, hi) = fminf(DG_D(s, hi), dv + l);
+      const float dv = DG_F(s, n);
+      // arcs into the bottom terminal write its entry, which this pass never reads
+      DG_F(s, lo) = fminf(DG_F(s, lo), dv);
+      DG_F(s, hi) = fminf(DG_F(s, hi), dv + l);
     }
   }
 }

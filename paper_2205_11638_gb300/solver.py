@@ -239,9 +239,12 @@ class Arena:
 
     def lb_seed(self, lam, M, stream=None):
         gl, gM = self.zeros(), self.zeros()
-        check(_lib.load().dg_lb_seed(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(gl), _ptr(gM)),
-              "dg_lb_seed")
+        self.lb_seed_into(lam, M, gl, gM, stream)
         return gl, gM
+
+    def lb_seed_into(self, lam, M, g_lam, g_M, stream=None):
+        check(_lib.load().dg_lb_seed(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(g_lam), _ptr(g_M)),
+              "dg_lb_seed")
 
     def graph(self, lam, M, omega=None, alpha=None, iters=1, lb_out=None, stream=None, **opt):
         return Graph(self, lam, M, omega, alpha, iters, lb_out, stream, self._opts(**opt))
@@ -251,16 +254,20 @@ class Arena:
 
     def backward(self, lam0, M0, omega, alpha, iters, ckpt_every, g_lamT, g_MT, stream=None, workspace=None):
         """Alg. 2 through ``iters`` iterations; returns (g_lam0, g_M0, g_omega, g_alpha)."""
+        outs = [self.zeros() for _ in range(4)]
+        self.backward_into(lam0, M0, omega, alpha, iters, ckpt_every, g_lamT, g_MT, outs, workspace, stream)
+        return tuple(outs)
+
+    def backward_into(self, lam0, M0, omega, alpha, iters, ckpt_every, g_lamT, g_MT, outs, workspace=None,
+                      stream=None):
         mode = 0 if omega is None else 1
         ws_bytes = self.backward_workspace_bytes(iters, ckpt_every)
         if workspace is None:
             workspace = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=self.device)
-        outs = [self.zeros() for _ in range(4)]
         check(_lib.load().dg_backward(self._h, _stream_handle(stream), _ptr(lam0), _ptr(M0), _ptr(omega),
                                       _ptr(alpha), mode, int(iters), int(ckpt_every), _ptr(g_lamT), _ptr(g_MT),
                                       *[_ptr(o) for o in outs], _ptr(workspace), int(workspace.numel()),
                                       ctypes.byref(self.options)), "dg_backward")
-        return tuple(outs)
 
 
 class DualIterate(torch.autograd.Function):
