@@ -82,7 +82,15 @@ typedef struct dg_options {
                             every k iterations (0 = never) */
   float omega;           /* damping of mode 0 (default 0.5 when 0) */
   int32_t num_threads;   /* host threads for dg_plan (0 = hardware concurrency) */
-  int32_t reserved[8];
+  int32_t host_mb_limit; /* host memory budget of dg_plan in MiB for the arena
+                            image (0 = none); exceeding it fails with
+                            DG_ENOMEM before the image is allocated */
+  int32_t chunk_rows;    /* rows per locality chunk before BDDs are sorted
+                            into tiles (default 16384) */
+  int32_t group_ratio_pct; /* a launch group keeps tiles whose shared-memory
+                              footprint is at least this percent of its largest
+                              (default 85) */
+  int32_t reserved[5];
 } dg_options;
 
 typedef struct dg_sizes {
@@ -247,6 +255,23 @@ dg_status dg_graph_create(dg_arena* arena, void* stream, float* lam, float* M, c
                           int32_t mode, int32_t iters, double* lb_out, const dg_options* opts, dg_graph_t** out);
 dg_status dg_graph_replay(dg_graph_t* g, void* stream);
 void dg_graph_destroy(dg_graph_t* g);
+
+/* Autotuner of the launch shapes, by coordinate descent on the time of one
+ * forward plus one backward sweep (CUDA events on stream, `reps` repetitions
+ * per candidate): first the number of concurrent streams (1, 2, 4), then for
+ * every launch group and direction the CTA size (1, 2 or 4 warps that fit),
+ * a change kept only when the whole pair gets faster by more than 0.5 %.  The
+ * choice is stored in the arena and used by every later call.  lam and M are
+ * work buffers (any finite state, e.g. from dg_init_lambda): their contents
+ * are undefined afterwards.  Synchronises the stream.  tuned_ms (nullable)
+ * receives the tuned time of one iteration's sweeps. */
+dg_status dg_autotune(dg_arena* arena, void* stream, float* lam, float* M, int32_t reps, float* tuned_ms);
+
+/* Waits until all work queued on stream has finished, for at most
+ * timeout_ms milliseconds (polling, no device-side wait).  DG_ETIMEOUT if the
+ * work is still running then (it keeps running; call again to wait more),
+ * DG_ECUDA if the stream reports an error. */
+dg_status dg_wait(void* stream, int32_t timeout_ms);
 
 /* Number of kernel launches one dg_iterate call with these arguments issues. */
 int32_t dg_iterate_launches(const dg_arena* arena, int32_t iters, int32_t want_lb, const dg_options* opts);

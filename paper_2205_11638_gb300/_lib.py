@@ -33,7 +33,8 @@ class dg_rows(ctypes.Structure):
 class dg_options(ctypes.Structure):
     _fields_ = [("tile_nodes", c_int32), ("tile_slots", c_int32), ("block_threads", c_int32),
                 ("renorm_every", c_int32), ("omega", c_float), ("num_threads", c_int32),
-                ("reserved", c_int32 * 8)]
+                ("host_mb_limit", c_int32), ("chunk_rows", c_int32), ("group_ratio_pct", c_int32),
+                ("reserved", c_int32 * 5)]
 
 
 class dg_sizes(ctypes.Structure):
@@ -79,6 +80,8 @@ SIGNATURES = {
     "dg_graph_replay": (c_int32, [P, P]),
     "dg_graph_destroy": (None, [P]),
     "dg_iterate_launches": (c_int32, [P, c_int32, c_int32, ctypes.POINTER(dg_options)]),
+    "dg_wait": (c_int32, [P, c_int32]),
+    "dg_autotune": (c_int32, [P, P, P, P, c_int32, P]),
 }
 
 _lib = None

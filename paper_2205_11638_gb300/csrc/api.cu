@@ -1,9 +1,11 @@
 // api.cu -- the C ABI of libdg (declared in include/dg.h): status codes,
 // two-phase build (host plan, device bind), the solver calls, the CUDA graph
 // of the iteration loop.
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 
 #include "kernels.h"
 
@@ -345,11 +347,92 @@ dg_status dg_iterate(dg_arena* ar, void* stream, float* lam, float* M, const flo
   return enqueue_iterate(ar, (cudaStream_t)stream, lam, M, omega, alpha, mode, iters, lb_out, opts);
 }
 
+dg_status dg_autotune(dg_arena* ar, void* stream, float* lam, float* M, int32_t reps, float* tuned_ms) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M) return fail(DG_EINVAL, "dg_autotune: null work buffers");
+  if (dg_status s = check_vectors("dg_autotune", lam, M)) return s;
+  reps = std::max(1, std::min(reps, 100));
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevArena& A = ar->dev;
+  SweepArgs a{};
+  a.lam = lam;
+  a.M = M;
+  a.omega0 = 0.5f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(DG_ECUDA, "dg_autotune: event creation failed");
+  auto timed = [&](auto&& body) -> float {
+    body();  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) body();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  launch_reduce_S(A, M, nullptr, nullptr, 0, false, st);
+  auto pair = [&] {
+    launch_sweep(kFwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+    launch_sweep(kBwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+  };
+  // start from the occupancy choice, made explicit
+  for (LaunchGroup& G : ar->groups) {
+    G.wpc_fwd = (int8_t)best_warps_per_cta((size_t)G.region_bytes0, 4, ar->cta_smem_cap);
+    G.wpc_bwd = (int8_t)best_warps_per_cta((size_t)G.region_bwd0, 4, ar->cta_smem_cap);
+  }
+  float best = 3.0e38f;
+  int bestn = kStreams;
+  for (int nstr : {1, 2, kStreams}) {
+    ar->streams.n = nstr;
+    const float ms = timed(pair);
+    if (ms < best) {
+      best = ms;
+      bestn = nstr;
+    }
+  }
+  ar->streams.n = bestn;
+  best = timed(pair);
+  for (LaunchGroup& G : ar->groups) {
+    for (int dir = 0; dir < 2; ++dir) {
+      int8_t& cur = dir == 0 ? G.wpc_fwd : G.wpc_bwd;
+      const size_t region = (size_t)(dir == 0 ? G.region_bytes0 : G.region_bwd0);
+      const int8_t keep = cur;
+      for (int w = 1; w <= 4; w *= 2) {
+        if (w == keep || region * w > ar->cta_smem_cap) continue;
+        cur = (int8_t)w;
+        const float ms = timed(pair);
+        if (ms < best * 0.995f) {
+          best = ms;
+          break;
+        }
+        cur = keep;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (tuned_ms) *tuned_ms = best;
+  return check_launch("dg_autotune");
+}
+
+dg_status dg_wait(void* stream, int32_t timeout_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+    if (e == cudaSuccess) return DG_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "dg_wait");
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms) return fail(DG_ETIMEOUT, "dg_wait: work still running after " + std::to_string(timeout_ms) + " ms");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
 int32_t dg_iterate_launches(const dg_arena* ar, int32_t iters, int32_t want_lb, const dg_options* opts) {
-  (void)ar;
   (void)opts;
-  int32_t l = 1 + 4 * iters;
-  if (want_lb) l += 2 + (iters == 0 ? 1 : 0);
+  const int32_t g = ar ? (int32_t)ar->groups.size() : 1;
+  int32_t l = 1 + iters * (2 * g + 2);
+  if (want_lb) l += 2 + (iters == 0 ? g : 0);
   return l;
 }
 

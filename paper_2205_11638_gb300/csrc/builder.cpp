@@ -258,7 +258,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   // element 32 n + b of the per-tile arrays.  Node numbers 0 and 1 stand for
   // the top and bottom terminals, the BDD's own nodes are numbered 2, 3, ...
   // level by level; child codes are node numbers (8 bits).
-  const int64_t kChunkRows = 16384;
+  const int64_t kChunkRows = opts && opts->chunk_rows > 0 ? opts->chunk_rows : 16384;
   std::vector<int64_t> order(m);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
@@ -280,6 +280,15 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   for (uint8_t w : width) max_width = std::max<int>(max_width, w);
 
   const int T = (int)((m + kWarp - 1) / kWarp);
+  if (opts && opts->host_mb_limit > 0) {
+    // host bytes of the arena image about to be built: child codes, slot
+    // arrays (descriptor, variable, row, CSR position), variable CSR
+    const double est = 2.0 * (double)num_nodes * 1.1 + 18.0 * (double)nnz * 1.1 + 8.0 * (double)nnz +
+                       16.0 * (double)n + 40.0 * (double)T;
+    if (est > (double)opts->host_mb_limit * 1048576.0)
+      return fail(DG_ENOMEM, "dg_plan: the arena image needs about " + std::to_string((long long)(est / 1048576.0)) +
+                                 " MiB of host memory, more than host_mb_limit");
+  }
   // tile t takes BDDs order[32 t .. 32 t + 31]; tiles are then laid out by
   // shared-memory footprint, largest first, so that tiles of one launch group
   // are contiguous (and the longest tiles start first)
@@ -358,13 +367,14 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   // launch groups: consecutive tiles whose footprints stay within 1/kGroupRatio
   // of the group's largest one
   {
-    const double kGroupRatio = 0.75;
+    const double kGroupRatio =
+        opts && opts->group_ratio_pct > 0 && opts->group_ratio_pct <= 100 ? opts->group_ratio_pct / 100.0 : 0.85;
     int32_t t0 = 0;
     size_t gmax = 0, gmax0 = 0;
     for (int t = 0; t < T; ++t) {
       const size_t r = sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1, P.tiles[t].ring);
       if (t > t0 && (double)r < kGroupRatio * (double)gmax) {
-        P.groups.push_back({t0, t, (int32_t)gmax, (int32_t)gmax0, 0, 0, 0, 0, 0});
+        P.groups.push_back({t0, t, (int32_t)gmax, (int32_t)gmax0, 0, 0, 0, 0, 0, 0, {0, 0}});
         t0 = t;
         gmax = 0;
         gmax0 = 0;
@@ -372,7 +382,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
       gmax = std::max(gmax, r);
       gmax0 = std::max(gmax0, sweep_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0, P.tiles[t].ring));
     }
-    if (T > 0) P.groups.push_back({t0, T, (int32_t)gmax, (int32_t)gmax0, 0, 0, 0, 0, 0});
+    if (T > 0) P.groups.push_back({t0, T, (int32_t)gmax, (int32_t)gmax0, 0, 0, 0, 0, 0, 0, {0, 0}});
     for (LaunchGroup& g : P.groups)
       for (int t = g.tile0; t < g.tile1; ++t) {
         g.region_bwd1 = std::max<int32_t>(g.region_bwd1, (int32_t)sweep_smem_bytes_bwd(P.tiles[t].nmax, P.tiles[t].nhops, 1));

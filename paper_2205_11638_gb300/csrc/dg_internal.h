@@ -84,7 +84,9 @@ struct LaunchGroup {
   int32_t region_bwd0;    // ... mode 0
   int64_t work;           // estimated cost: sum over tiles of 32 * nmax * nhops
   int32_t stream;         // stream of the fork/join set the group runs on
-  int32_t pad;
+  int8_t wpc_fwd;         // tuned warps per CTA (0: choose by occupancy)
+  int8_t wpc_bwd;
+  int8_t pad[2];
 };
 
 // Tiles of one adjoint launch (the sweep's launch groups with the adjoint's

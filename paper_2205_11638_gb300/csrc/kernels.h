@@ -29,7 +29,11 @@ struct StreamSet {
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kStreams - 1] = {};
   bool ready = false;
-  cudaStream_t of(int k) const { return k == 0 || !ready ? main : aux[k - 1]; }
+  int n = kStreams;  // streams in use (1: everything on main)
+  cudaStream_t of(int k) const {
+    const int j = n > 0 ? k % n : 0;
+    return j == 0 || !ready ? main : aux[j - 1];
+  }
   void begin() const;  // fork
   void end() const;    // join
 };

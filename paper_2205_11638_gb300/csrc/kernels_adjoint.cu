@@ -396,7 +396,7 @@ cudaError_t set_adjoint_smem_limit(size_t bytes) {
 template <int FWD, int MODE>
 static void launch_adj(const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups, size_t cap,
                        const StreamSet& ss) {
-  const bool fork = num_groups > 1;
+  const bool fork = num_groups > 1 && ss.ready;
   if (fork) ss.begin();
   for (int g = 0; g < num_groups; ++g) {
     const AdjGroup& G = groups[g];

@@ -176,14 +176,14 @@ int best_warps_per_cta(size_t region, int max_wpc, size_t cta_cap) {
 }
 
 void StreamSet::begin() const {
-  if (!ready) return;
+  if (!ready || n <= 1) return;
   cudaEventRecord(fork, main);
-  for (int k = 0; k < kStreams - 1; ++k) cudaStreamWaitEvent(aux[k], fork, 0);
+  for (int k = 0; k < n - 1; ++k) cudaStreamWaitEvent(aux[k], fork, 0);
 }
 
 void StreamSet::end() const {
-  if (!ready) return;
-  for (int k = 0; k < kStreams - 1; ++k) {
+  if (!ready || n <= 1) return;
+  for (int k = 0; k < n - 1; ++k) {
     cudaEventRecord(join[k], aux[k]);
     cudaStreamWaitEvent(main, join[k], 0);
   }
@@ -192,7 +192,7 @@ void StreamSet::end() const {
 template <int KIND, int MODE>
 static void launch_groups(const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
                           int num_groups, const StreamSet& ss) {
-  const bool fork = num_groups > 1;
+  const bool fork = num_groups > 1 && ss.ready;
   if (fork) ss.begin();
   for (int g = 0; g < num_groups; ++g) {
     const LaunchGroup& G = groups[g];
@@ -200,7 +200,11 @@ static void launch_groups(const DevArena& A, const SweepArgs& a, int threads, co
                                                 : (MODE == 1 ? G.region_bytes : G.region_bytes0));
     int wpc = threads / kWarp;
     if (wpc > 4) wpc = 4;  // __launch_bounds__(128)
-    wpc = best_warps_per_cta(region, wpc, g_cta_smem_cap);
+    const int tuned = KIND == kBwd ? G.wpc_bwd : G.wpc_fwd;
+    if (tuned > 0 && region * tuned <= g_cta_smem_cap)
+      wpc = tuned;
+    else
+      wpc = best_warps_per_cta(region, wpc, g_cta_smem_cap);
     const int nt = G.tile1 - G.tile0;
     dim3 grid((nt + wpc - 1) / wpc), block(wpc * kWarp);
     k_sweep<KIND, MODE><<<grid, block, region * wpc, fork ? ss.of(G.stream) : ss.main>>>(A, a, (int)region, G.tile0,

@@ -26,8 +26,12 @@ def _ptr(t):
     return ctypes.c_void_p(t.ctypes.data)
 
 
-def make_options(tile_nodes=0, tile_slots=0, block_threads=0, renorm_every=0, omega=0.0, num_threads=0):
+def make_options(tile_nodes=0, tile_slots=0, block_threads=0, renorm_every=0, omega=0.0, num_threads=0,
+                 host_mb_limit=0, chunk_rows=0, group_ratio_pct=0):
     o = dg_options()
+    o.host_mb_limit = int(host_mb_limit)
+    o.chunk_rows = int(chunk_rows)
+    o.group_ratio_pct = int(group_ratio_pct)
     o.tile_nodes = int(tile_nodes)
     o.tile_slots = int(tile_slots)
     o.block_threads = int(block_threads)
@@ -268,6 +272,11 @@ class Arena:
                                       _ptr(alpha), mode, int(iters), int(ckpt_every), _ptr(g_lamT), _ptr(g_MT),
                                       *[_ptr(o) for o in outs], _ptr(workspace), int(workspace.numel()),
                                       ctypes.byref(self.options)), "dg_backward")
+
+
+def wait(stream=None, timeout_ms=1000):
+    """dg_wait: bounded host wait for the stream's work; returns the status."""
+    return int(_lib.load().dg_wait(_stream_handle(stream), int(timeout_ms)))
 
 
 class DualIterate(torch.autograd.Function):

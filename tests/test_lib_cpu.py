@@ -128,3 +128,24 @@ def test_tile_budgets_respected():
         P = solver.plan(prob, tile_nodes=tn, tile_slots=ts)
         assert P.sizes.smem_bytes <= 227 * 1024
         assert P.sizes.num_nodes_padded >= P.sizes.num_nodes
+
+
+def test_host_memory_budget_fails_with_enomem():
+    """Allocator-failure injection on the host: a budget below the arena
+    image makes dg_plan fail with DG_ENOMEM, before anything is allocated."""
+    prob = workloads.independent_set(n=20_000, seed=3)
+    with pytest.raises(_lib.DgError) as e:
+        solver.plan(prob, host_mb_limit=1)
+    assert e.value.status == _lib.DG_ENOMEM
+    solver.plan(prob, host_mb_limit=512)  # a sufficient budget passes
+
+
+def test_calls_on_missing_arena_fail_cleanly():
+    """Null arena / null state: status codes, no crash, no CUDA call needed."""
+    lib = _lib.load()
+    assert lib.dg_iterate(None, None, None, None, None, None, 0, 1, None, None) == _lib.DG_ESTATE
+    assert lib.dg_lower_bound(None, None, None, None, None, None) == _lib.DG_ESTATE
+    assert lib.dg_backward(None, None, None, None, None, None, 0, 1, 1, None, None, None, None, None, None,
+                           None, 0, None) == _lib.DG_ESTATE
+    assert lib.dg_graph_replay(None, None) == _lib.DG_EINVAL
+    assert b"null" in lib.dg_last_error()
