@@ -247,6 +247,32 @@ dg_status dg_backward(dg_arena* arena, void* stream, const float* lam0, const fl
                       const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,
                       void* workspace, size_t ws_bytes, const dg_options* opts);
 
+/* --- DOGE-Train's updates around the solver ------------------------------ */
+
+/* Non-parametric update (eq. 2, Sec. 3.4):
+ *   lambda_ij += theta_ij - (1/|J_i|) sum_{k in J_i} theta_ik
+ * in place; keeps sum_j lambda_ij unchanged (dual feasibility). */
+dg_status dg_nonparam_update(dg_arena* arena, void* stream, float* lam, const float* theta);
+
+/* Adjoint of dg_nonparam_update: the gradient of lambda passes through
+ * unchanged and g_theta = g_lam - mean over J_i of g_lam. */
+dg_status dg_nonparam_backward(dg_arena* arena, void* stream, const float* g_lam, float* g_theta);
+
+/* Output transforms of the parameter predictor (Alg. 3): per variable
+ * alpha_i. = softmax(alpha_hat_i.) over J_i, omega = sigmoid(omega_hat),
+ * theta_i. = theta_hat_i. - mean over J_i.  Any (input, output) pair may be
+ * NULL to skip it.  Padding slots of the outputs are left unchanged. */
+dg_status dg_param_transform(dg_arena* arena, void* stream, const float* alpha_hat, const float* omega_hat,
+                             const float* theta_hat, float* alpha, float* omega, float* theta);
+
+/* Adjoint of dg_param_transform given its outputs alpha, omega and the
+ * gradients g_alpha, g_omega, g_theta: g_alpha_hat = alpha (g_alpha -
+ * sum_k alpha_k g_alpha_k) per variable, g_omega_hat = g_omega omega
+ * (1 - omega), g_theta_hat = g_theta - mean over J_i.  NULL pairs skipped. */
+dg_status dg_param_transform_backward(dg_arena* arena, void* stream, const float* alpha, const float* omega,
+                                      const float* g_alpha, const float* g_omega, const float* g_theta,
+                                      float* g_alpha_hat, float* g_omega_hat, float* g_theta_hat);
+
 /* --- CUDA graph of the iteration loop ------------------------------------ */
 
 /* Captures `iters` iterations of dg_iterate (same arguments) into a CUDA

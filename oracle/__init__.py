@@ -61,6 +61,9 @@ def _load():
     lib.orc_lb_seed.argtypes = [P, P, P, P, P]
     lib.orc_minimiser.argtypes = [P, i64, P, ctypes.c_int, ctypes.c_int, P]
     lib.orc_backward.argtypes = [P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P]
+    lib.orc_nonparam_update.argtypes = [P, P, P]
+    lib.orc_param_transform.argtypes = [P, P, P, P, P, P, P]
+    lib.orc_param_transform_backward.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.orc_last_error.restype = ctypes.c_char_p
     _lib = lib
     del dp
@@ -198,6 +201,26 @@ class Oracle:
         x = np.zeros(len(lam_row), np.int32)
         _lib.orc_minimiser(self._h, int(j), _p(lam_row), int(h), int(beta), _p(x))
         return x
+
+    def nonparam_update(self, lam, theta):
+        """eq. 2 on a copy of lam."""
+        lam = np.array(lam, dtype=np.float64)
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        _lib.orc_nonparam_update(self._h, _p(lam), _p(theta))
+        return lam
+
+    def param_transform(self, alpha_hat, omega_hat, theta_hat):
+        """Alg. 3 output transforms; returns (alpha, omega, theta)."""
+        ins = [np.ascontiguousarray(x, dtype=np.float64) for x in (alpha_hat, omega_hat, theta_hat)]
+        outs = [np.zeros(self.num_slots) for _ in range(3)]
+        _lib.orc_param_transform(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
+        return tuple(outs)
+
+    def param_transform_backward(self, alpha, omega, g_alpha, g_omega, g_theta):
+        ins = [np.ascontiguousarray(x, dtype=np.float64) for x in (alpha, omega, g_alpha, g_omega, g_theta)]
+        outs = [np.zeros(self.num_slots) for _ in range(3)]
+        _lib.orc_param_transform_backward(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
+        return tuple(outs)
 
     def backward(self, lam0, M0, omega, alpha, iters, g_lamT, g_MT):
         """Alg. 2 through ``iters`` iterations; returns (g_lam0, g_M0, g_omega, g_alpha)."""

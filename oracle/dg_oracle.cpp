@@ -18,6 +18,10 @@
 //     the min-marginal formula via shortest paths              (App. B)
 //   * the loss L(lambda) = sum_j E^j and its gradient, the minimising
 //     assignment of each subproblem                            (Sec. 3.5, eq. 3)
+//   * the non-parametric update of eq. 2                        (Sec. 3.4)
+//   * the output transforms of the parameter predictor: softmax of the
+//     averaging weights over J_i, sigmoid of the damping, centring of theta
+//                                                               (Sec. 3.5, Alg. 3)
 //
 // Readings where the paper is silent or garbled (each one is also listed in
 // the design notes of the repository):
@@ -614,6 +618,55 @@ void orc_backward(void* p, const double* lam0, const double* M0, const double* o
     }
     std::copy(gl.begin(), gl.end(), g_lam0);
     std::copy(gM.begin(), gM.end(), g_M0);
+}
+
+// Non-parametric update (eq. 2): lambda_ij += theta_ij - mean_{k in J_i} theta_ik.
+void orc_nonparam_update(void* p, double* lam, const double* theta) {
+  Problem& P = *static_cast<Problem*>(p);
+  std::vector<double> sum(P.n, 0.0);
+  for (size_t s = 0; s < P.col.size(); ++s) sum[P.col[s]] += theta[s];
+  for (size_t s = 0; s < P.col.size(); ++s) lam[s] += theta[s] - sum[P.col[s]] / P.deg[P.col[s]];
+}
+
+// Output transforms of Alg. 3: alpha_i. = softmax(alpha_hat_i.) over J_i,
+// omega = sigmoid(omega_hat), theta_i. = theta_hat_i. - mean over J_i.
+void orc_param_transform(void* p, const double* alpha_hat, const double* omega_hat, const double* theta_hat,
+                         double* alpha, double* omega, double* theta) {
+  Problem& P = *static_cast<Problem*>(p);
+  const size_t N = P.col.size();
+  std::vector<double> mx(P.n, -INF), z(P.n, 0.0), tsum(P.n, 0.0);
+  for (size_t s = 0; s < N; ++s) mx[P.col[s]] = std::max(mx[P.col[s]], alpha_hat[s]);
+  for (size_t s = 0; s < N; ++s) {
+    z[P.col[s]] += std::exp(alpha_hat[s] - mx[P.col[s]]);
+    tsum[P.col[s]] += theta_hat[s];
+  }
+  for (size_t s = 0; s < N; ++s) {
+    const int i = P.col[s];
+    alpha[s] = std::exp(alpha_hat[s] - mx[i]) / z[i];
+    omega[s] = 1.0 / (1.0 + std::exp(-omega_hat[s]));
+    theta[s] = theta_hat[s] - tsum[i] / P.deg[i];
+  }
+}
+
+// Backpropagation through orc_param_transform: the Jacobian of the softmax
+// of a variable's weights, the derivative of the sigmoid, and the centring
+// (its own adjoint).
+void orc_param_transform_backward(void* p, const double* alpha, const double* omega, const double* g_alpha,
+                                  const double* g_omega, const double* g_theta, double* g_alpha_hat,
+                                  double* g_omega_hat, double* g_theta_hat) {
+  Problem& P = *static_cast<Problem*>(p);
+  const size_t N = P.col.size();
+  std::vector<double> dot(P.n, 0.0), gsum(P.n, 0.0);
+  for (size_t s = 0; s < N; ++s) {
+    dot[P.col[s]] += alpha[s] * g_alpha[s];
+    gsum[P.col[s]] += g_theta[s];
+  }
+  for (size_t s = 0; s < N; ++s) {
+    const int i = P.col[s];
+    g_alpha_hat[s] = alpha[s] * (g_alpha[s] - dot[i]);
+    g_omega_hat[s] = g_omega[s] * omega[s] * (1.0 - omega[s]);
+    g_theta_hat[s] = g_theta[s] - gsum[i] / P.deg[i];
+  }
 }
 
 }  // extern "C"

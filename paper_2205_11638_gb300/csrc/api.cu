@@ -528,6 +528,40 @@ dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* 
   return check_launch("dg_lb_seed");
 }
 
+dg_status dg_nonparam_update(dg_arena* ar, void* stream, float* lam, const float* theta) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !theta) return fail(DG_EINVAL, "dg_nonparam_update: null pointer");
+  launch_nonparam(ar->dev, lam, theta, (cudaStream_t)stream);
+  return check_launch("dg_nonparam_update");
+}
+
+dg_status dg_nonparam_backward(dg_arena* ar, void* stream, const float* g_lam, float* g_theta) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!g_lam || !g_theta) return fail(DG_EINVAL, "dg_nonparam_backward: null pointer");
+  launch_center(ar->dev, g_lam, g_theta, (cudaStream_t)stream);
+  return check_launch("dg_nonparam_backward");
+}
+
+dg_status dg_param_transform(dg_arena* ar, void* stream, const float* alpha_hat, const float* omega_hat,
+                             const float* theta_hat, float* alpha, float* omega, float* theta) {
+  if (dg_status s = check_state(ar)) return s;
+  if ((!alpha_hat) != (!alpha) || (!omega_hat) != (!omega) || (!theta_hat) != (!theta))
+    return fail(DG_EINVAL, "dg_param_transform: every input needs its output");
+  launch_param_transform(ar->dev, alpha_hat, omega_hat, theta_hat, alpha, omega, theta, (cudaStream_t)stream);
+  return check_launch("dg_param_transform");
+}
+
+dg_status dg_param_transform_backward(dg_arena* ar, void* stream, const float* alpha, const float* omega,
+                                      const float* g_alpha, const float* g_omega, const float* g_theta,
+                                      float* g_alpha_hat, float* g_omega_hat, float* g_theta_hat) {
+  if (dg_status s = check_state(ar)) return s;
+  if ((g_alpha_hat && (!alpha || !g_alpha)) || (g_omega_hat && (!omega || !g_omega)) || (g_theta_hat && !g_theta))
+    return fail(DG_EINVAL, "dg_param_transform_backward: missing input for a requested gradient");
+  launch_param_transform_bwd(ar->dev, alpha, omega, g_alpha, g_omega, g_theta, g_alpha_hat, g_omega_hat, g_theta_hat,
+                             (cudaStream_t)stream);
+  return check_launch("dg_param_transform_backward");
+}
+
 dg_status dg_graph_create(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
                           int32_t mode, int32_t iters, double* lb_out, const dg_options* opts, dg_graph_t** out) {
   if (dg_status s = check_state(ar)) return s;

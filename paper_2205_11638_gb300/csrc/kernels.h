@@ -78,6 +78,14 @@ void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cuda
 // out_slot[q] = v[variable of q] (0 for padding slots)
 void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st);
 
+// eq. 2 and the output transforms of Alg. 3 (kernels_params.cu)
+void launch_nonparam(const DevArena& A, float* lam, const float* theta, cudaStream_t st);
+void launch_center(const DevArena& A, const float* x, float* out, cudaStream_t st);
+void launch_param_transform(const DevArena& A, const float* ah, const float* wh, const float* th, float* alpha,
+                            float* omega, float* theta, cudaStream_t st);
+void launch_param_transform_bwd(const DevArena& A, const float* alpha, const float* omega, const float* ga,
+                                const float* gw, const float* gt, float* gah, float* gwh, float* gth, cudaStream_t st);
+
 // dg_lower_bound with its intermediates in a static device array (noalloc.cu).
 dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, int num_groups, int threads,
                               const StreamSet& ss, const float* lam, const float* M, double* lb);

@@ -250,6 +250,30 @@ class Arena:
         check(_lib.load().dg_lb_seed(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(g_lam), _ptr(g_M)),
               "dg_lb_seed")
 
+    # -- DOGE-Train's updates around the solver (eq. 2, Alg. 3) ------------
+    def nonparam_update(self, lam, theta, stream=None):
+        check(_lib.load().dg_nonparam_update(self._h, _stream_handle(stream), _ptr(lam), _ptr(theta)),
+              "dg_nonparam_update")
+
+    def nonparam_backward(self, g_lam, stream=None):
+        g = self.zeros()
+        check(_lib.load().dg_nonparam_backward(self._h, _stream_handle(stream), _ptr(g_lam), _ptr(g)),
+              "dg_nonparam_backward")
+        return g
+
+    def param_transform(self, alpha_hat, omega_hat, theta_hat, stream=None):
+        outs = [self.zeros() if x is not None else None for x in (alpha_hat, omega_hat, theta_hat)]
+        check(_lib.load().dg_param_transform(self._h, _stream_handle(stream), _ptr(alpha_hat), _ptr(omega_hat),
+                                             _ptr(theta_hat), *[_ptr(o) for o in outs]), "dg_param_transform")
+        return tuple(outs)
+
+    def param_transform_backward(self, alpha, omega, g_alpha, g_omega, g_theta, stream=None):
+        outs = [self.zeros() if g is not None else None for g in (g_alpha, g_omega, g_theta)]
+        check(_lib.load().dg_param_transform_backward(self._h, _stream_handle(stream), _ptr(alpha), _ptr(omega),
+                                                      _ptr(g_alpha), _ptr(g_omega), _ptr(g_theta),
+                                                      *[_ptr(o) for o in outs]), "dg_param_transform_backward")
+        return tuple(outs)
+
     def graph(self, lam, M, omega=None, alpha=None, iters=1, lb_out=None, stream=None, **opt):
         return Graph(self, lam, M, omega, alpha, iters, lb_out, stream, self._opts(**opt))
 
@@ -328,6 +352,45 @@ class LowerBound(torch.autograd.Function):
             return gl * w, gM * w, None
         scale = g.float()[A.slot_instance()]
         return gl * scale, gM * scale, None
+
+
+class NonParamUpdate(torch.autograd.Function):
+    """lam + theta - mean_{J_i} theta (eq. 2), on the device."""
+
+    @staticmethod
+    def forward(ctx, lam, theta, arena):
+        ctx.arena = arena
+        out = lam.detach().clone()
+        arena.nonparam_update(out, theta.detach().contiguous())
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous().float()
+        return g, ctx.arena.nonparam_backward(g), None
+
+
+class ParamTransform(torch.autograd.Function):
+    """(alpha_hat, omega_hat, theta_hat) -> (softmax over J_i, sigmoid, centred)
+    as in Alg. 3, on the device."""
+
+    @staticmethod
+    def forward(ctx, alpha_hat, omega_hat, theta_hat, arena):
+        ctx.arena = arena
+        a, w, t = arena.param_transform(alpha_hat.detach().contiguous(), omega_hat.detach().contiguous(),
+                                        theta_hat.detach().contiguous())
+        ctx.save_for_backward(a, w)
+        return a, w, t
+
+    @staticmethod
+    def backward(ctx, ga, gw, gt):
+        a, w = ctx.saved_tensors
+        A = ctx.arena
+        ga = A.zeros() if ga is None else ga.contiguous().float()
+        gw = A.zeros() if gw is None else gw.contiguous().float()
+        gt = A.zeros() if gt is None else gt.contiguous().float()
+        gah, gwh, gth = A.param_transform_backward(a, w, ga, gw, gt)
+        return gah, gwh, gth, None
 
 
 class Graph:
