@@ -273,6 +273,16 @@ dg_status dg_param_transform_backward(dg_arena* arena, void* stream, const float
                                       const float* g_alpha, const float* g_omega, const float* g_theta,
                                       float* g_alpha_hat, float* g_omega_hat, float* g_theta_hat);
 
+/* Smoothed subproblems of the feature table (App. C), read as the soft-min
+ *   E_a^j(lambda) = -a log sum_{x in X_j} exp(-<lambda_.j, x> / a)
+ * (the paper prints a soft-max; as the smoothing of E^j = min it must tend to
+ * E^j when a -> 0), computed by log-sum-exp over the BDD's paths in FP32.
+ * marginals (arena order, float32[num_slots]) receives the gradient
+ * dE_a^j / dlambda_ij = P(x_i = 1) under p(x) ~ exp(-<lambda, x>/a);
+ * E_per_row (nullable, float32[m], original row order) receives E_a^j. */
+dg_status dg_smoothed_dual(dg_arena* arena, void* stream, const float* lam, float a, float* E_per_row,
+                           float* marginals);
+
 /* --- CUDA graph of the iteration loop ------------------------------------ */
 
 /* Captures `iters` iterations of dg_iterate (same arguments) into a CUDA

@@ -64,6 +64,7 @@ def _load():
     lib.orc_nonparam_update.argtypes = [P, P, P]
     lib.orc_param_transform.argtypes = [P, P, P, P, P, P, P]
     lib.orc_param_transform_backward.argtypes = [P, P, P, P, P, P, P, P, P]
+    lib.orc_smoothed.argtypes = [P, P, ctypes.c_double, P, P]
     lib.orc_last_error.restype = ctypes.c_char_p
     _lib = lib
     del dp
@@ -221,6 +222,14 @@ class Oracle:
         outs = [np.zeros(self.num_slots) for _ in range(3)]
         _lib.orc_param_transform_backward(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
         return tuple(outs)
+
+    def smoothed(self, lam, a):
+        """Smoothed subproblems (soft-min reading): (E_a per row, marginals per slot)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        E = np.zeros(self.m)
+        mg = np.zeros(self.num_slots)
+        _lib.orc_smoothed(self._h, _p(lam), float(a), _p(E), _p(mg))
+        return E, mg
 
     def backward(self, lam0, M0, omega, alpha, iters, g_lamT, g_MT):
         """Alg. 2 through ``iters`` iterations; returns (g_lam0, g_M0, g_omega, g_alpha)."""

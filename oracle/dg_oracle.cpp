@@ -22,6 +22,13 @@
 //   * the output transforms of the parameter predictor: softmax of the
 //     averaging weights over J_i, sigmoid of the damping, centring of theta
 //                                                               (Sec. 3.5, Alg. 3)
+//   * the smoothed subproblems of the feature table and their gradients
+//                                                    (App. C, hand-crafted features)
+//
+//   R12 the smoothed subproblem is printed as alpha log sum_x exp(<lambda,x>/alpha),
+//       a soft-max; as the smoothing of a minimisation it is read as
+//       E_a(lambda) = -a log sum_{x in X_j} exp(-<lambda, x>/a), which tends to
+//       E^j as a -> 0; its gradient is the vector of marginals P(x_i = 1).
 //
 // Readings where the paper is silent or garbled (each one is also listed in
 // the design notes of the repository):
@@ -666,6 +673,50 @@ void orc_param_transform_backward(void* p, const double* alpha, const double* om
     g_alpha_hat[s] = alpha[s] * (g_alpha[s] - dot[i]);
     g_omega_hat[s] = g_omega[s] * omega[s] * (1.0 - omega[s]);
     g_theta_hat[s] = g_theta[s] - gsum[i] / P.deg[i];
+  }
+}
+
+// Smoothed subproblems (reading R12) by log-sum-exp over the BDD's paths:
+// B(v) = log sum over v-T paths of exp(-cost/a), F(v) the same over r-v
+// paths; log Z = B(root); E_a = -a log Z; the marginal of slot h is
+// sum over level-h nodes with a 1-arc of exp(F(v) - lambda_h/a + B(s1(v)) - log Z).
+static double lse(double x, double y) {
+  if (x == -INF) return y;
+  if (y == -INF) return x;
+  const double m = std::max(x, y);
+  return m + std::log(std::exp(x - m) + std::exp(y - m));
+}
+
+void orc_smoothed(void* p, const double* lam, double a, double* E_a, double* marg) {
+  Problem& P = *static_cast<Problem*>(p);
+  for (int64_t j = 0; j < P.m; ++j) {
+    const Bdd& B = P.bdd[j];
+    const double* lj = lam + P.row_ptr[j];
+    std::vector<double> bw(B.lo.size(), -INF), fw(B.lo.size(), -INF);
+    auto child_b = [&](int h, int ch) { return ch == TOP ? 0.0 : (ch == BOT ? -INF : bw[B.level_start[h + 1] + ch]); };
+    for (int h = B.k - 1; h >= 0; --h)
+      for (int v = B.level_start[h]; v < B.level_start[h + 1]; ++v)
+        bw[v] = lse(child_b(h, B.lo[v]), B.hi[v] == BOT ? -INF : -lj[h] / a + child_b(h, B.hi[v]));
+    const double logZ = bw[0];
+    if (E_a) E_a[j] = -a * logZ;
+    fw[0] = 0.0;
+    for (int h = 0; h < B.k; ++h) {
+      double acc = -INF;
+      for (int v = B.level_start[h]; v < B.level_start[h + 1]; ++v) {
+        if (B.hi[v] != BOT) acc = lse(acc, fw[v] - lj[h] / a + child_b(h, B.hi[v]));
+        if (h + 1 < B.k) {
+          if (B.lo[v] >= 0) {
+            int w = B.level_start[h + 1] + B.lo[v];
+            fw[w] = lse(fw[w], fw[v]);
+          }
+          if (B.hi[v] >= 0) {
+            int w = B.level_start[h + 1] + B.hi[v];
+            fw[w] = lse(fw[w], fw[v] - lj[h] / a);
+          }
+        }
+      }
+      if (marg) marg[P.row_ptr[j] + h] = std::exp(acc - logZ);
+    }
   }
 }
 

@@ -81,6 +81,7 @@ SIGNATURES = {
     "dg_graph_destroy": (None, [P]),
     "dg_iterate_launches": (c_int32, [P, c_int32, c_int32, ctypes.POINTER(dg_options)]),
     "dg_wait": (c_int32, [P, c_int32]),
+    "dg_smoothed_dual": (c_int32, [P, P, P, c_float, P, P]),
     "dg_nonparam_update": (c_int32, [P, P, P, P]),
     "dg_nonparam_backward": (c_int32, [P, P, P, P]),
     "dg_param_transform": (c_int32, [P, P, P, P, P, P, P, P]),

@@ -528,6 +528,16 @@ dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* 
   return check_launch("dg_lb_seed");
 }
 
+dg_status dg_smoothed_dual(dg_arena* ar, void* stream, const float* lam, float a, float* E_per_row, float* marginals) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !marginals) return fail(DG_EINVAL, "dg_smoothed_dual: null pointer");
+  if (!(a > 0.0f)) return fail(DG_EINVAL, "dg_smoothed_dual: smoothing factor must be positive");
+  if (dg_status s = check_vectors("dg_smoothed_dual", lam, marginals)) return s;
+  launch_smoothed(ar->dev, lam, a, E_per_row, marginals, ar->groups.data(), (int)ar->groups.size(),
+                  streams_for(ar, (cudaStream_t)stream));
+  return check_launch("dg_smoothed_dual");
+}
+
 dg_status dg_nonparam_update(dg_arena* ar, void* stream, float* lam, const float* theta) {
   if (dg_status s = check_state(ar)) return s;
   if (!lam || !theta) return fail(DG_EINVAL, "dg_nonparam_update: null pointer");

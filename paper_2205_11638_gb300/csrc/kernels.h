@@ -78,6 +78,10 @@ void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cuda
 // out_slot[q] = v[variable of q] (0 for padding slots)
 void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st);
 
+// smoothed subproblems (soft-min reading) and their marginals
+void launch_smoothed(const DevArena& A, const float* lam, float a_s, float* E_a, float* marg, const LaunchGroup* groups,
+                     int num_groups, const StreamSet& ss);
+
 // eq. 2 and the output transforms of Alg. 3 (kernels_params.cu)
 void launch_nonparam(const DevArena& A, float* lam, const float* theta, cudaStream_t st);
 void launch_center(const DevArena& A, const float* x, float* out, cudaStream_t st);

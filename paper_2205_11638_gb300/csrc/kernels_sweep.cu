@@ -18,6 +18,8 @@
 
 namespace dg {
 
+static size_t g_cta_smem_cap = 227 * 1024;
+
 template <int KIND, int MODE>
 __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int region_bytes, int tile0, int tile1) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -134,6 +136,85 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
   }
 }
 
+// log(exp(x) + exp(y)) with -inf as the empty sum.
+__device__ __forceinline__ float lse2(float x, float y) {
+  const float m = fmaxf(x, y);
+  if (m == -f_inf()) return m;
+  return m + log1pf(expf(-fabsf(x - y)));
+}
+
+// Smoothed subproblems (the feature table's smoothed dual, read as the
+// soft-min E_a = -a log sum_{x in X_j} exp(-<lambda, x>/a)) and their
+// gradients, the marginals P(x_i = 1), by log-sum-exp over the BDD paths:
+// B(v) over v-T paths, F(v) over r-v paths, log Z = B(root).
+__global__ void __launch_bounds__(128) k_smoothed(DevArena A, const float* lam, float a_s, float* E_a, float* marg,
+                                                  int region_bytes, int tile0, int tile1) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = tile0 + blockIdx.x * (blockDim.x >> 5) + warp;
+  if (tile >= tile1) return;
+  const Tile T = A.tiles[tile];
+  TileSmem s = carve<0, false>(smem + (size_t)warp * region_bytes, T);
+  load_tile<false, 0>(A, T, s, lam, nullptr, nullptr, lane);
+  const int64_t sbase = T.slot_base;
+  const float inv_a = 1.0f / a_s;
+  DG_F(s, kBotCode) = -f_inf();  // B of the terminals: log 1 = 0 for top, log 0 for bottom
+  for (int h = s.nh - 1; h >= 0; --h) {
+    const uint32_t ds = s.desc[h * kWarp + lane];
+    const int w = desc_width(ds);
+    if (w == 0) continue;
+    const int fn = desc_first(ds);
+    const float wgt = -s.lam[h * kWarp + lane] * inv_a;
+    for (int r = 0; r < w; ++r) {
+      const int n = fn + r;
+      const uint32_t c = node_code(s, n, lane);
+      DG_F(s, n) = lse2(DG_F(s, c & 0xFFu), wgt + DG_F(s, c >> 8));
+    }
+  }
+  if (desc_width(s.desc[lane]) == 0) return;
+  const float logZ = DG_F(s, 2);
+  if (E_a) E_a[__ldg(A.slot_row + sbase + lane)] = -a_s * logZ;
+  DG_W(s, 2) = 0.0f;
+  for (int h = 0; h < s.nh; ++h) {
+    const uint32_t ds = s.desc[h * kWarp + lane];
+    const int w = desc_width(ds);
+    if (w == 0) break;
+    const int fn = desc_first(ds);
+    const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
+    const int wn = desc_width(dn), fnn = desc_first(dn);
+    const float wgt = -s.lam[h * kWarp + lane] * inv_a;
+    for (int r = 0; r < wn; ++r) DG_W(s, fnn + r) = -f_inf();
+    float acc = -f_inf();
+    for (int r = 0; r < w; ++r) {
+      const int n = fn + r;
+      const uint32_t c = node_code(s, n, lane);
+      const uint32_t lo = c & 0xFFu, hi = c >> 8;
+      const float f = DG_W(s, n);
+      acc = lse2(acc, f + wgt + DG_F(s, hi));
+      if (wn > 0) {
+        DG_W(s, lo) = lse2(DG_W(s, lo), f);  // bottom's entry is scratch
+        DG_W(s, hi) = lse2(DG_W(s, hi), f + wgt);
+      }
+    }
+    marg[sbase + h * kWarp + lane] = expf(acc - logZ);
+  }
+}
+
+void launch_smoothed(const DevArena& A, const float* lam, float a_s, float* E_a, float* marg, const LaunchGroup* groups,
+                     int num_groups, const StreamSet& ss) {
+  const bool fork = num_groups > 1 && ss.ready;
+  if (fork) ss.begin();
+  for (int g = 0; g < num_groups; ++g) {
+    const LaunchGroup& G = groups[g];
+    const size_t region = (size_t)G.region_bwd0;
+    const int wpc = best_warps_per_cta(region, 4, g_cta_smem_cap);
+    const int nt = G.tile1 - G.tile0;
+    k_smoothed<<<(nt + wpc - 1) / wpc, wpc * kWarp, region * wpc, fork ? ss.of(G.stream) : ss.main>>>(
+        A, lam, a_s, E_a, marg, (int)region, G.tile0, G.tile1);
+  }
+  if (fork) ss.end();
+}
+
 template <int KIND>
 static cudaError_t set_attr(int b) {
   cudaError_t e = cudaFuncSetAttribute(k_sweep<KIND, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
@@ -143,7 +224,8 @@ static cudaError_t set_attr(int b) {
 
 cudaError_t set_sweep_smem_limit(size_t bytes) {
   const int b = (int)bytes;
-  cudaError_t e = set_attr<kFwd>(b);
+  cudaError_t e = cudaFuncSetAttribute(k_smoothed, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = set_attr<kFwd>(b);
   if (e == cudaSuccess) e = set_attr<kBwd>(b);
   if (e == cudaSuccess) e = set_attr<kMinMarg>(b);
   if (e == cudaSuccess) e = set_attr<kEnergy>(b);
@@ -151,7 +233,6 @@ cudaError_t set_sweep_smem_limit(size_t bytes) {
   return e;
 }
 
-static size_t g_cta_smem_cap = 227 * 1024;
 void set_cta_smem_cap(size_t bytes) { g_cta_smem_cap = bytes; }
 
 // Warps per CTA for a per-warp slice of `region` bytes: the CTA size (1, 2

@@ -250,6 +250,14 @@ class Arena:
         check(_lib.load().dg_lb_seed(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(g_lam), _ptr(g_M)),
               "dg_lb_seed")
 
+    def smoothed_dual(self, lam, a, stream=None):
+        """(E_a per row, marginals per slot) of the smoothed subproblems."""
+        E = torch.zeros(self.m, dtype=torch.float32, device=self.device)
+        mg = self.zeros()
+        check(_lib.load().dg_smoothed_dual(self._h, _stream_handle(stream), _ptr(lam), float(a), _ptr(E), _ptr(mg)),
+              "dg_smoothed_dual")
+        return E, mg
+
     # -- DOGE-Train's updates around the solver (eq. 2, Alg. 3) ------------
     def nonparam_update(self, lam, theta, stream=None):
         check(_lib.load().dg_nonparam_update(self._h, _stream_handle(stream), _ptr(lam), _ptr(theta)),

@@ -96,3 +96,18 @@ def test_doge_round_end_to_end_gradients(seed):
     assert abs(float(lb) - O.lower_bound(lT, MT)) < 1e-4 * max(1.0, abs(float(lb)))
     for leaf, wv in zip(leaves, want):
         np.testing.assert_allclose(_np(A.to_csr(leaf.grad)), wv, atol=1e-4)
+
+
+@pytest.mark.parametrize("a", [1.0, 10.0, 100.0])
+def test_smoothed_dual_vs_oracle(a):
+    """Smoothed-dual features for the three smoothing factors of the feature
+    table, FP32 log-sum-exp on the GPU against the FP64 oracle."""
+    prob = workloads.matching_quadratic(L=60, R=60, pairs=3000, seed=8)
+    O = oracle.Oracle(prob)
+    A = solver.plan(prob).bind()
+    rng = np.random.default_rng(int(a))
+    lam = _f32(rng.normal(size=O.num_slots) * 2)
+    E, mg = A.smoothed_dual(A.from_csr(lam), a)
+    oE, omg = O.smoothed(lam, a)
+    np.testing.assert_allclose(_np(E), oE, rtol=1e-5, atol=1e-5 * a)
+    np.testing.assert_allclose(_np(A.to_csr(mg)), omg, atol=1e-4)
