@@ -61,22 +61,34 @@ __global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
   const int4 ch = __ldg(A.lb_chunks + blockIdx.x);
   float hi = 0.f, lo = 0.f;
   double unc = 0.0;  // uncovered variables: float64 costs
-  for (int x = ch.z + threadIdx.x; x < ch.w; x += blockDim.x) {
-    float v;
-    if (ch.y == 0) {
-      v = A.E[x];
-    } else {
-      const int deg = __ldg(A.var_ptr + x + 1) - __ldg(A.var_ptr + x);
-      if (deg == 0) {
-        unc += fmin(0.0, A.c[x]);
-        continue;
+  constexpr int kU = 4;  // loads of kU elements are issued before their sums
+  for (int x0 = ch.z + threadIdx.x; x0 < ch.w; x0 += kU * blockDim.x) {
+    float v[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int x = x0 + u * blockDim.x;
+      ok[u] = x < ch.w;
+      v[u] = 0.f;
+      if (ok[u]) {
+        if (ch.y == 0) {
+          v[u] = A.E[x];
+        } else if (__ldg(A.invdeg + x) > 0.f) {
+          v[u] = fminf(0.f, A.S[x]);
+        } else {
+          unc += fmin(0.0, A.c[x]);
+          ok[u] = false;
+        }
       }
-      v = fminf(0.f, A.S[x]);
     }
-    const float s = hi + v;
-    const float bp = s - hi;
-    lo += (hi - (s - bp)) + (v - bp);
-    hi = s;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (!ok[u]) continue;
+      const float s = hi + v[u];
+      const float bp = s - hi;
+      lo += (hi - (s - bp)) + (v[u] - bp);
+      hi = s;
+    }
   }
   double acc = (double)hi + (double)lo + unc;
   __shared__ double red[8];
