@@ -9,7 +9,7 @@
 
 #include <vector_types.h>
 
-#include "../../include/dg.h"
+#include "dg.h"
 
 namespace dg {
 

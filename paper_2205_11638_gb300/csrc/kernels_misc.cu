@@ -90,15 +90,31 @@ __global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
       hi = s;
     }
   }
-  double acc = (double)hi + (double)lo + unc;
-  __shared__ double red[8];
+  // float-float tree over the block (TwoSum at every step), one conversion
+  // to float64 per block: FP64 arithmetic is slow on this part
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+    const float l2 = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+    const float s = hi + h2;
+    const float bp = s - hi;
+    lo = lo + l2 + ((hi - (s - bp)) + (h2 - bp));
+    hi = s;
+  }
+  __shared__ float rh[8], rl[8];
+  __shared__ double ru[8];
+  if ((threadIdx.x & 31) == 0) {
+    rh[threadIdx.x >> 5] = hi;
+    rl[threadIdx.x >> 5] = lo;
+  }
+  // uncovered variables (float64 costs) are rare: reduce them separately
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) unc += __shfl_down_sync(0xFFFFFFFFu, unc, o);
+  if ((threadIdx.x & 31) == 0) ru[threadIdx.x >> 5] = unc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)rh[w] + (double)rl[w] + ru[w];
     A.lb_part[blockIdx.x] = t;
   }
 }

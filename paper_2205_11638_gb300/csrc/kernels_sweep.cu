@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
       const int wn = desc_width(dn), fnn = desc_first(dn);
       float b0 = f_inf(), b1 = f_inf();
+      #pragma unroll 2
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
@@ -66,7 +67,9 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         a.M[sbase + q] = Mn;
       }
       if (wn > 0) {
+        #pragma unroll 2
         for (int r = 0; r < wn; ++r) DG_R(s, fnn + r) = f_inf();
+        #pragma unroll 2
         for (int r = 0; r < w; ++r) {
           const int n = fn + r;
           const uint32_t c = node_code(s, n, lane);
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       if (w == 0) continue;
       const int fn = desc_first(ds);
       float b0 = f_inf(), b1 = f_inf();
+      #pragma unroll 2
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const float ln = l - Mn + slot_avg<MODE>(s, q);
       a.lam[sbase + q] = ln;
       a.M[sbase + q] = Mn;
+      #pragma unroll 2
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
@@ -165,6 +170,7 @@ __global__ void __launch_bounds__(128) k_smoothed(DevArena A, const float* lam, 
     if (w == 0) continue;
     const int fn = desc_first(ds);
     const float wgt = -s.lam[h * kWarp + lane] * inv_a;
+    #pragma unroll 2
     for (int r = 0; r < w; ++r) {
       const int n = fn + r;
       const uint32_t c = node_code(s, n, lane);
@@ -183,8 +189,10 @@ __global__ void __launch_bounds__(128) k_smoothed(DevArena A, const float* lam, 
     const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
     const int wn = desc_width(dn), fnn = desc_first(dn);
     const float wgt = -s.lam[h * kWarp + lane] * inv_a;
+    #pragma unroll 2
     for (int r = 0; r < wn; ++r) DG_W(s, fnn + r) = -f_inf();
     float acc = -f_inf();
+    #pragma unroll 2
     for (int r = 0; r < w; ++r) {
       const int n = fn + r;
       const uint32_t c = node_code(s, n, lane);

@@ -163,6 +163,7 @@ __device__ __forceinline__ void lane_cost_to_top(TileSmem& s, int lane) {
     if (w == 0) continue;
     const int fn = desc_first(ds);
     const float l = s.lam[h * kWarp + lane];
+    #pragma unroll 2
     for (int r = 0; r < w; ++r) {
       const int n = fn + r;
       const uint32_t c = node_code(s, n, lane);
@@ -183,7 +184,9 @@ __device__ __forceinline__ void lane_cost_from_root(TileSmem& s, int lane) {
     if (wn == 0) break;
     const int fn = desc_first(ds), fnn = desc_first(dn);
     const float l = s.lam[h * kWarp + lane];
+    #pragma unroll 2
     for (int r = 0; r < wn; ++r) DG_F(s, fnn + r) = f_inf();
+    #pragma unroll 2
     for (int r = 0; r < w; ++r) {
       const int n = fn + r;
       const uint32_t c = node_code(s, n, lane);

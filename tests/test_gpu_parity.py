@@ -237,3 +237,11 @@ def test_renorm_keeps_invariant_in_fp64():
     c = torch.as_tensor(prob["c"], device=A.device)
     cov = torch.bincount(col, minlength=n) > 0
     assert (tot - c)[cov].abs().max().item() < 2e-6
+
+
+def test_config4_full_batch_per_instance_bounds():
+    """All 64 uneven instances of the batching configuration in one arena:
+    lambda after one iteration and every instance's bound after 10."""
+    prob, kinds = workloads.batched_mix(num=64)
+    assert len(prob["inst_row_ptr"]) == 65
+    _check_iterations(prob, 1, 10)
