@@ -150,6 +150,12 @@ void dg_destroy(dg_arena* arena);
 dg_status dg_get_sizes(const dg_plan_t* plan, dg_sizes* sizes);
 dg_status dg_get_stats(const dg_arena* arena, dg_stats* stats);
 
+/* Launch group g of the plan's sweeps (0 <= g < num_launch_groups): its tile
+ * range [tile0, tile1), the shared memory one warp uses in a forward sweep
+ * (mode 0) and the stream of the fork/join set it runs on. */
+dg_status dg_launch_group(const dg_plan_t* plan, int32_t g, int32_t* tile0, int32_t* tile1, int32_t* region_bytes,
+                          int32_t* stream);
+
 /* slot_to_csr[q] = CSR position (row_ptr[j] + h) of arena slot q, or -1 for
  * padding (host array of num_slots entries). */
 dg_status dg_slot_map(const dg_plan_t* plan, int64_t* slot_to_csr);

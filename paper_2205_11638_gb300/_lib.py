@@ -63,6 +63,7 @@ SIGNATURES = {
     "dg_get_sizes": (c_int32, [P, ctypes.POINTER(dg_sizes)]),
     "dg_get_stats": (c_int32, [P, ctypes.POINTER(dg_stats)]),
     "dg_slot_map": (c_int32, [P, P]),
+    "dg_launch_group": (c_int32, [P, c_int32, P, P, P, P]),
     "dg_bdd_export": (c_int32, [P, c_int64, P, P, P, ctypes.POINTER(c_int32)]),
     "dg_init_lambda": (c_int32, [P, P, P, P]),
     "dg_iterate": (c_int32, [P, P, P, P, P, P, c_int32, c_int32, P, ctypes.POINTER(dg_options)]),

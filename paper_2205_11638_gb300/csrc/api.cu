@@ -164,6 +164,18 @@ dg_status dg_get_sizes(const dg_plan_t* plan, dg_sizes* sizes) {
   return DG_OK;
 }
 
+dg_status dg_launch_group(const dg_plan_t* plan, int32_t g, int32_t* tile0, int32_t* tile1, int32_t* region_bytes,
+                          int32_t* stream) {
+  if (!plan) return fail(DG_EINVAL, "dg_launch_group: null plan");
+  if (g < 0 || g >= (int32_t)plan->p.groups.size()) return fail(DG_EINVAL, "dg_launch_group: group out of range");
+  const LaunchGroup& G = plan->p.groups[g];
+  if (tile0) *tile0 = G.tile0;
+  if (tile1) *tile1 = G.tile1;
+  if (region_bytes) *region_bytes = G.region_bytes0;
+  if (stream) *stream = G.stream;
+  return DG_OK;
+}
+
 dg_status dg_slot_map(const dg_plan_t* plan, int64_t* out) {
   if (!plan || !out) return fail(DG_EINVAL, "dg_slot_map: null argument");
   std::memcpy(out, plan->p.slot_to_csr.data(), plan->p.slot_to_csr.size() * sizeof(int64_t));

@@ -99,6 +99,15 @@ class Plan:
         check(lib.dg_bdd_export(self._h, int(j), _ptr(ls), _ptr(lo), _ptr(hi), ctypes.byref(nn)), "dg_bdd_export")
         return ls, lo, hi
 
+    def launch_groups(self):
+        """[(tile0, tile1, per-warp shared bytes, stream)] of the sweep launches."""
+        out = []
+        for g in range(int(self.sizes.num_launch_groups)):
+            v = [ctypes.c_int32() for _ in range(4)]
+            check(_lib.load().dg_launch_group(self._h, g, *[ctypes.byref(x) for x in v]), "dg_launch_group")
+            out.append(tuple(x.value for x in v))
+        return out
+
     def bind(self, device=None, stream=None) -> "Arena":
         return Arena(self, device, stream)
 
