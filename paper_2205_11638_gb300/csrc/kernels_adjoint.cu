@@ -83,7 +83,7 @@ __device__ __forceinline__ AdjSmem carve_adj(unsigned char* p, const Tile& T) {
   p += (size_t)ns * 2;
   s.amin = (uint16_t*)p;
   p += (size_t)ns * 2;
-  s.code = (uint16_t*)p;
+  s.code = (uint16_t*)p - 2 * kWarp;  // biased: element 32 n + lane is node number n
   return s;
 }
 
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   const int64_t sb = T.slot_base;
 
   // ---- staging ----------------------------------------------------------
-  copy_async(s.code, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+  copy_async(s.code + 2 * kWarp, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
   copy_async(s.desc, A.desc + sb, ns * 2, lane);
   copy_async(s.lam, a.lam_old + sb, ns * 4, lane);
   copy_async(s.gl, a.g_lam + sb, ns * 4, lane);

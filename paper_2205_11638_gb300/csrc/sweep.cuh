@@ -32,7 +32,8 @@ struct TileSmem {
   float* om;       // [32 * nh] omega_ij (mode 1)
   float* al;       // [32 * nh] alpha_ij (mode 1)
   uint16_t* desc;  // [32 * nh]
-  uint16_t* code;  // [32 * (nmax - 2)] child codes (lo | hi << 8), lane-interleaved
+  uint16_t* code;       // child codes, biased: element 32 n + lane is node number n
+  uint16_t* code_base;  // [32 * (nmax - 2)] the staged codes of nodes 2 .. nmax-1
   int nmax, nh, rmask;
 };
 
@@ -63,7 +64,8 @@ __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
   }
   s.desc = (uint16_t*)p;
   p += (size_t)ns * 2;
-  s.code = (uint16_t*)p;
+  s.code_base = (uint16_t*)p;
+  s.code = s.code_base - 2 * kWarp;
   return s;
 }
 
@@ -72,13 +74,13 @@ __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
 // DG_R the ring element of node number n >= 2 (the two live levels always
 // occupy fewer than `ring` consecutive node numbers).
 #define DG_F(s, n) (s).full[(n) * kWarp + lane]
-#define DG_R(s, n) (s).ring[((((int)(n)) - 2) & (s).rmask) * kWarp + lane]
+#define DG_R(s, n) (s).ring[(((int)(n)) & (s).rmask) * kWarp + lane]
 // second whole array (backward sweeps): element of node number n
 #define DG_W(s, n) (s).ring[(n) * kWarp + lane]
 
 // Child codes (lo | hi << 8) of node number n >= 2 of my BDD.
 __device__ __forceinline__ uint32_t node_code(const uint16_t* code, int n, int lane) {
-  return code[(n - 2) * kWarp + lane];
+  return code[n * kWarp + lane];
 }
 __device__ __forceinline__ uint32_t node_code(const TileSmem& s, int n, int lane) {
   return node_code(s.code, n, lane);
@@ -112,7 +114,7 @@ template <bool WITH_S, int MODE>
 __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, TileSmem& s, const float* lam,
                                           const float* omega, const float* alpha, int lane) {
   const int ns = s.nh * kWarp;
-  copy_async(s.code, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+  copy_async(s.code_base, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
   copy_async(s.desc, A.desc + T.slot_base, ns * 2, lane);
   copy_async(s.lam, lam + T.slot_base, ns * 4, lane);
   if (WITH_S) {
