@@ -238,6 +238,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   cp(P.off.inst_var_ptr, P.inst_var_ptr.data(), P.inst_var_ptr.size() * 4);
   cp(P.off.lb_chunks, P.lb_chunks.data(), P.lb_chunks.size() * 4);
   cp(P.off.inst_chunk_ptr, P.inst_chunk_ptr.data(), P.inst_chunk_ptr.size() * 4);
+  cp(P.off.inst_unc, P.inst_unc.data(), P.inst_unc.size() * 8);
   cudaError_t e = cudaMemcpyAsync(arena_dev, h.data(), image, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)arena_dev + P.off.S, 0, P.off.total - P.off.S, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -287,6 +288,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.inst_var_ptr = (const int32_t*)(b + P.off.inst_var_ptr);
   A.lb_chunks = (const int4*)(b + P.off.lb_chunks);
   A.inst_chunk_ptr = (const int32_t*)(b + P.off.inst_chunk_ptr);
+  A.inst_unc = (const double*)(b + P.off.inst_unc);
   A.S = (float*)(b + P.off.S);
   A.Sbar = (float*)(b + P.off.Sbar);
   A.E = (float*)(b + P.off.E);

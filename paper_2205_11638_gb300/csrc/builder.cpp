@@ -445,6 +445,13 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     }
     P.inst_chunk_ptr[k + 1] = (int32_t)(P.lb_chunks.size() / 4);
   }
+  // variables no row covers keep their cost: their term of the bound is the
+  // constant min(0, c_i) (their S_i is an empty sum, 0, so the kernels may add
+  // min(0, S_i) = 0 for them as for every other variable)
+  P.inst_unc.assign(ni, 0.0);
+  for (int k = 0; k < ni; ++k)
+    for (int32_t i = P.inst_var_ptr[k]; i < P.inst_var_ptr[k + 1]; ++i)
+      if (P.var_ptr[i + 1] == P.var_ptr[i]) P.inst_unc[k] += std::min(0.0, P.c[i]);
   const int num_chunks = (int)(P.lb_chunks.size() / 4);
 
   // ---- 5. arena offsets ----------------------------------------------------
@@ -467,6 +474,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.inst_var_ptr = put((size_t)(ni + 1) * 4);
   P.off.lb_chunks = put((size_t)num_chunks * 16);
   P.off.inst_chunk_ptr = put((size_t)(ni + 1) * 4);
+  P.off.inst_unc = put((size_t)ni * 8);
   P.off.S = put((size_t)n * 4);
   P.off.Sbar = put((size_t)n * 4);
   P.off.E = put((size_t)m * 4);

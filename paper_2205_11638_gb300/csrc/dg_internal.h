@@ -61,6 +61,7 @@ struct DevArena {
   const int32_t* inst_var_ptr;
   const int4* lb_chunks;    // {instance, kind (0 rows, 1 vars), begin, end}
   const int32_t* inst_chunk_ptr;
+  const double* inst_unc;   // per instance: sum of min(0, c_i) over variables no row covers
   float* S;                 // scratch: per-variable sum of M (snapshot)
   float* Sbar;              // scratch: S_i / |J_i| (the mode-0 averaging term)
   float* E;                 // scratch: E^j per original row
@@ -116,6 +117,7 @@ struct Plan {
   std::vector<int32_t> inst_var_ptr;
   std::vector<int32_t> lb_chunks;  // 4 ints per chunk
   std::vector<int32_t> inst_chunk_ptr;
+  std::vector<double> inst_unc;    // per instance: sum of min(0, c_i) over its uncovered variables
   std::vector<int64_t> slot_to_csr;
   // canonical BDDs (for dg_bdd_export): per CSR slot the level width, per
   // node the child ranks (-2 bottom, -1 top)
@@ -125,7 +127,7 @@ struct Plan {
   // byte offsets of every array inside the arena
   struct Off {
     size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, c, invdeg, inst_row_ptr, inst_var_ptr,
-        lb_chunks, inst_chunk_ptr, S, Sbar, E, lb_part, total;
+        lb_chunks, inst_chunk_ptr, inst_unc, S, Sbar, E, lb_part, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels
   size_t smem_adjoint = 0; // dynamic smem of the adjoint kernels

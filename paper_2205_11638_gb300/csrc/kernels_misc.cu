@@ -18,16 +18,44 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
   if (i >= A.n) return;
   const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
   float s = 0.f;
+  if (!RENORM) {
+    // most variables sit in a handful of rows: the slot numbers of up to four
+    // positions, then their M values, are loaded before any of them is added
+    // (same order of additions as the plain loop)
+    int k = b;
+    for (; k + 4 <= e; k += 4) {
+      const int q0 = __ldg(A.var_slots + k), q1 = __ldg(A.var_slots + k + 1);
+      const int q2 = __ldg(A.var_slots + k + 2), q3 = __ldg(A.var_slots + k + 3);
+      const float m0 = M[q0], m1 = M[q1], m2 = M[q2], m3 = M[q3];
+      s += m0;
+      s += m1;
+      s += m2;
+      s += m3;
+    }
+    const int r = e - k;  // 0..3
+    const int q0 = r > 0 ? __ldg(A.var_slots + k) : 0;
+    const int q1 = r > 1 ? __ldg(A.var_slots + k + 1) : 0;
+    const int q2 = r > 2 ? __ldg(A.var_slots + k + 2) : 0;
+    const float m0 = r > 0 ? M[q0] : 0.f;
+    const float m1 = r > 1 ? M[q1] : 0.f;
+    const float m2 = r > 2 ? M[q2] : 0.f;
+    if (r > 0) s += m0;
+    if (r > 1) s += m1;
+    if (r > 2) s += m2;
+    A.S[i] = s;
+    A.Sbar[i] = __ldg(A.invdeg + i) * s;
+    return;
+  }
   double tot = 0.0;
   for (int k = b; k < e; ++k) {
     const int q = __ldg(A.var_slots + k);
     const float mk = M[q];
     s += mk;
-    if (RENORM) tot += (double)lam[q] + (double)mk;
+    tot += (double)lam[q] + (double)mk;
   }
   A.S[i] = s;
   A.Sbar[i] = __ldg(A.invdeg + i) * s;
-  if (RENORM && e > b) {
+  if (e > b) {
     const double r = A.c[i] - tot;
     const float inv = __ldg(A.invdeg + i);
     for (int k = b; k < e; ++k) {
@@ -52,7 +80,8 @@ __global__ void k_init(DevArena A, float* lam, float* M) {
 }
 
 // One partial sum per chunk: rows contribute E^j, variables min(0, S_i)
-// (or min(0, c_i) when no row covers them).  FP64 arithmetic is slow on this
+// (variables no row covers add min(0, c_i), a constant per instance that
+// k_lb_final adds).  FP64 arithmetic is slow on this
 // part, so every thread accumulates its float32 terms with Knuth's TwoSum
 // (an error-free transformation: the running sum and its exact rounding
 // error, both float32), and only the per-thread results are combined in
@@ -60,30 +89,21 @@ __global__ void k_init(DevArena A, float* lam, float* M) {
 __global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
   const int4 ch = __ldg(A.lb_chunks + blockIdx.x);
   float hi = 0.f, lo = 0.f;
-  double unc = 0.0;  // uncovered variables: float64 costs
+  // variables no row covers have S_i = 0 (an empty sum), so min(0, S_i) adds
+  // nothing for them; their cost term is the per-instance constant inst_unc
+  const bool rows = ch.y == 0;
+  const float* src = rows ? A.E : A.S;
   constexpr int kU = 4;  // loads of kU elements are issued before their sums
   for (int x0 = ch.z + threadIdx.x; x0 < ch.w; x0 += kU * blockDim.x) {
     float v[kU];
-    bool ok[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int x = x0 + u * blockDim.x;
-      ok[u] = x < ch.w;
-      v[u] = 0.f;
-      if (ok[u]) {
-        if (ch.y == 0) {
-          v[u] = A.E[x];
-        } else if (__ldg(A.invdeg + x) > 0.f) {
-          v[u] = fminf(0.f, A.S[x]);
-        } else {
-          unc += fmin(0.0, A.c[x]);
-          ok[u] = false;
-        }
-      }
+      const float y = x < ch.w ? src[x] : 0.f;
+      v[u] = rows ? y : fminf(0.f, y);
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      if (!ok[u]) continue;
       const float s = hi + v[u];
       const float bp = s - hi;
       lo += (hi - (s - bp)) + (v[u] - bp);
@@ -102,19 +122,14 @@ __global__ void __launch_bounds__(256) k_lb_partial(DevArena A) {
     hi = s;
   }
   __shared__ float rh[8], rl[8];
-  __shared__ double ru[8];
   if ((threadIdx.x & 31) == 0) {
     rh[threadIdx.x >> 5] = hi;
     rl[threadIdx.x >> 5] = lo;
   }
-  // uncovered variables (float64 costs) are rare: reduce them separately
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) unc += __shfl_down_sync(0xFFFFFFFFu, unc, o);
-  if ((threadIdx.x & 31) == 0) ru[threadIdx.x >> 5] = unc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)rh[w] + (double)rl[w] + ru[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)rh[w] + (double)rl[w];
     A.lb_part[blockIdx.x] = t;
   }
 }
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(256) k_lb_final(DevArena A, double* lb) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    lb[k] = s;
+    lb[k] = s + A.inst_unc[k];
   }
 }
 

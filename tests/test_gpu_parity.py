@@ -245,3 +245,29 @@ def test_config4_full_batch_per_instance_bounds():
     prob, kinds = workloads.batched_mix(num=64)
     assert len(prob["inst_row_ptr"]) == 65
     _check_iterations(prob, 1, 10)
+
+
+def test_batched_uncovered_variables_per_instance():
+    """Variables that no row covers add min(0, c_i) to their own instance's
+    bound only (Def. 2 with the unary term): three instances, uncovered
+    variables of negative and positive cost in the first and last."""
+    rng = np.random.default_rng(17)
+    insts = []
+    for k, extra in enumerate(((-3.0, 2.0), (), (0.5, -7.25, -1.0))):
+        n0 = 12
+        rows = []
+        for r in workloads.random_rows(40, kmax=5, n=n0, seed=300 + k):
+            try:
+                oracle.Oracle(workloads.single_rows_problem([r], n0, np.zeros(n0)))
+                rows.append(r)
+            except oracle.OracleError:
+                pass
+        c = np.concatenate([rng.normal(size=n0), np.asarray(extra, dtype=np.float64)])
+        insts.append(workloads.single_rows_problem(rows[:10], n0 + len(extra), c))
+    prob = workloads.concat(insts)
+    A, O, lam, M = _check_iterations(prob, 1, 30)
+    got = A.lower_bound(lam, M).cpu().numpy()
+    ol, oM = O.init_lambda()
+    ol, oM = O.iterate(ol, oM, 0.5, None, 30)
+    want = O.lower_bound(ol, oM, per_instance=True)[1]
+    np.testing.assert_allclose(got, want, rtol=TOL_LB, atol=TOL_LB)
