@@ -282,9 +282,9 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   const int T = (int)((m + kWarp - 1) / kWarp);
   if (opts && opts->host_mb_limit > 0) {
     // host bytes of the arena image about to be built: child codes, slot
-    // arrays (descriptor, variable, row, CSR position), variable CSR
+    // arrays (descriptor, variable, row, CSR position), variable CSR and ELL
     const double est = 2.0 * (double)num_nodes * 1.1 + 18.0 * (double)nnz * 1.1 + 8.0 * (double)nnz +
-                       16.0 * (double)n + 40.0 * (double)T;
+                       (16.0 + 4.0 * kEll) * (double)n + 40.0 * (double)T;
     if (est > (double)opts->host_mb_limit * 1048576.0)
       return fail(DG_ENOMEM, "dg_plan: the arena image needs about " + std::to_string((long long)(est / 1048576.0)) +
                                  " MiB of host memory, more than host_mb_limit");
@@ -427,6 +427,12 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     for (int64_t s = 0; s < nnz; ++s) P.var_slots[cur[R->col[s]]++] = (int32_t)slot_of_csr[s];
   }
   P.c.assign(R->c, R->c + n);
+  P.var_ell.assign((size_t)kEll * n, -1);
+  for (int32_t i = 0; i < n; ++i) {
+    const int d = P.var_ptr[i + 1] - P.var_ptr[i];
+    for (int r = 0; r < std::min(d, kEll); ++r) P.var_ell[(size_t)r * n + i] = P.var_slots[P.var_ptr[i] + r];
+    if (d > kEll) P.var_ell[(size_t)(kEll - 1) * n + i] = -2 - P.var_ell[(size_t)(kEll - 1) * n + i];
+  }
   P.invdeg.assign(n, 0.0f);
   for (int32_t i = 0; i < n; ++i) {
     int d = P.var_ptr[i + 1] - P.var_ptr[i];
@@ -468,6 +474,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.slot_row = put(num_slots * 4);
   P.off.var_ptr = put((size_t)(n + 1) * 4);
   P.off.var_slots = put((size_t)nnz * 4);
+  P.off.var_ell = put((size_t)kEll * n * 4);
   P.off.c = put((size_t)n * 8);
   P.off.invdeg = put((size_t)n * 4);
   P.off.inst_row_ptr = put((size_t)(ni + 1) * 8);

@@ -22,6 +22,12 @@ constexpr int kMaxNodesPerBdd = 254;
 constexpr int kWarp = 32;
 constexpr int kMaxWidth = 32;  // nodes of one BDD level
 constexpr int kStreams = 4;    // streams one sweep's launch groups run on
+// The first kEll slots of every variable are also stored column by column
+// (var_ell[r * n + i], ELLPACK layout) so that the S reduction reads them
+// without first reading var_ptr; -1 marks "no slot", and a variable with more
+// than kEll slots stores its last ELL entry as -2 - slot, the rest coming
+// from var_slots[var_ptr[i] + kEll ..].
+constexpr int kEll = 4;
 
 // One tile = up to 32 BDDs swept by one warp, BDD b by lane b.  Per-tile
 // arrays are interleaved by lane: slot (h, b) is slot_base + 32 h + b (its
@@ -55,6 +61,7 @@ struct DevArena {
   const int32_t* slot_row;  // original row of a slot, -1 for padding
   const int32_t* var_ptr;   // CSR over variables: slots of variable i
   const int32_t* var_slots; // arena slots, grouped by variable, rows ascending
+  const int32_t* var_ell;   // [kEll * n] the first kEll slots of each variable (see kEll)
   const double* c;          // objective, float64[n]
   const float* invdeg;      // 1/|J_i| (0 for uncovered variables)
   const int64_t* inst_row_ptr;
@@ -110,7 +117,7 @@ struct Plan {
   std::vector<uint16_t> desc;
   std::vector<uint16_t> lohi8;
   std::vector<int32_t> slot_var, slot_row;
-  std::vector<int32_t> var_ptr, var_slots;
+  std::vector<int32_t> var_ptr, var_slots, var_ell;
   std::vector<double> c;
   std::vector<float> invdeg;
   std::vector<int64_t> inst_row_ptr;
@@ -126,7 +133,7 @@ struct Plan {
   std::vector<int8_t> lo8, hi8;
   // byte offsets of every array inside the arena
   struct Off {
-    size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, c, invdeg, inst_row_ptr, inst_var_ptr,
+    size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, c, invdeg, inst_row_ptr, inst_var_ptr,
         lb_chunks, inst_chunk_ptr, inst_unc, S, Sbar, E, lb_part, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels

@@ -118,14 +118,15 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   __syncwarp();
   {
     int* sv = reinterpret_cast<int*>(s.tmp);
+    const uint64_t pol = l2_evict_last();
     for (int q = lane; q < ns; q += kWarp) {
       const int v = sv[q];
       if (!a.seed_M) s.md[q] = 0.0f;
       if (v >= 0) {
-        cp_async4(s.S + q, a.S_in + v);
-        if (MODE == 0) cp_async4(s.al + q, A.invdeg + v);
+        cp_async4(s.S + q, a.S_in + v, pol);
+        if (MODE == 0) cp_async4(s.al + q, A.invdeg + v, pol);
         if (a.sdot_next)
-          cp_async4(s.tmp + q, a.sdot_next + v);
+          cp_async4(s.tmp + q, a.sdot_next + v, pol);
         else
           s.tmp[q] = 0.0f;
       } else {

@@ -16,36 +16,31 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
                                                    const float* __restrict__ alpha, int mode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
-  const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
   float s = 0.f;
   if (!RENORM) {
-    // most variables sit in a handful of rows: the slot numbers of up to four
-    // positions, then their M values, are loaded before any of them is added
-    // (same order of additions as the plain loop)
-    int k = b;
-    for (; k + 4 <= e; k += 4) {
-      const int q0 = __ldg(A.var_slots + k), q1 = __ldg(A.var_slots + k + 1);
-      const int q2 = __ldg(A.var_slots + k + 2), q3 = __ldg(A.var_slots + k + 3);
-      const float m0 = M[q0], m1 = M[q1], m2 = M[q2], m3 = M[q3];
-      s += m0;
-      s += m1;
-      s += m2;
-      s += m3;
+    // the first kEll slots come from the ELL columns (coalesced, no var_ptr
+    // needed), all loaded before their M values, which are all loaded before
+    // the first addition; the order of additions is the plain loop's
+    int q[kEll];
+#pragma unroll
+    for (int r = 0; r < kEll; ++r) q[r] = __ldg(A.var_ell + (int64_t)r * A.n + i);
+    const bool more = q[kEll - 1] <= -2;
+    if (more) q[kEll - 1] = -2 - q[kEll - 1];
+    float mv[kEll];
+#pragma unroll
+    for (int r = 0; r < kEll; ++r) mv[r] = q[r] >= 0 ? M[q[r]] : 0.f;
+#pragma unroll
+    for (int r = 0; r < kEll; ++r)
+      if (q[r] >= 0) s += mv[r];
+    if (more) {
+      const int e = __ldg(A.var_ptr + i + 1);
+      for (int k = __ldg(A.var_ptr + i) + kEll; k < e; ++k) s += M[__ldg(A.var_slots + k)];
     }
-    const int r = e - k;  // 0..3
-    const int q0 = r > 0 ? __ldg(A.var_slots + k) : 0;
-    const int q1 = r > 1 ? __ldg(A.var_slots + k + 1) : 0;
-    const int q2 = r > 2 ? __ldg(A.var_slots + k + 2) : 0;
-    const float m0 = r > 0 ? M[q0] : 0.f;
-    const float m1 = r > 1 ? M[q1] : 0.f;
-    const float m2 = r > 2 ? M[q2] : 0.f;
-    if (r > 0) s += m0;
-    if (r > 1) s += m1;
-    if (r > 2) s += m2;
     A.S[i] = s;
     A.Sbar[i] = __ldg(A.invdeg + i) * s;
     return;
   }
+  const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
   double tot = 0.0;
   for (int k = b; k < e; ++k) {
     const int q = __ldg(A.var_slots + k);

@@ -86,15 +86,33 @@ __device__ __forceinline__ uint32_t node_code(const TileSmem& s, int n, int lane
   return node_code(s.code, n, lane);
 }
 
-// Asynchronous global -> shared copies (cp.async): 16 B for the streamed
-// tile arrays, 4 B for the gathers of per-variable terms.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+// L2 eviction priorities.  A sweep streams its tiles' arrays (child codes,
+// descriptors, lambda, ...) through L2 once, several times the L2's size,
+// while the per-variable terms it gathers (24 MB for 6 M variables) are hit
+// again and again at random: the streamed copies are marked evict_first and
+// the gathers evict_last, so the stream does not push the gathered array out.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Asynchronous global -> shared copies (cp.async) with an L2 policy: 16 B for
+// the streamed tile arrays, 4 B for the gathers of per-variable terms.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint64_t pol) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, uint64_t pol) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -102,7 +120,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes, int lane) {
   char* d = reinterpret_cast<char*>(dst);
   const char* g = reinterpret_cast<const char*>(src);
-  for (int o = lane * 16; o < bytes; o += kWarp * 16) cp_async16(d + o, g + o);
+  const uint64_t pol = l2_evict_first();
+  for (int o = lane * 16; o < bytes; o += kWarp * 16) cp_async16(d + o, g + o, pol);
 }
 
 // Warp-cooperative staging of the tile: child codes, slot descriptors,
@@ -132,11 +151,12 @@ __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, Tile
   if (WITH_S) {
     const float* src = MODE == 1 ? A.S : A.Sbar;
     int* sv = reinterpret_cast<int*>(s.sg);
+    const uint64_t pol = l2_evict_last();
 #pragma unroll 4
     for (int q = lane; q < ns; q += kWarp) {
       const int v = sv[q];
       if (v >= 0)
-        cp_async4(s.sg + q, src + v);
+        cp_async4(s.sg + q, src + v, pol);
       else
         s.sg[q] = 0.0f;
     }
