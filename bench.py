@@ -248,9 +248,9 @@ def _batched_measurement(args, solver, torch, iters=50, ck=10):
     # fwd + adjoint (lower-bound loss) on the batch vs per instance
     def fwd_adj(S, l0, m0):
         l, m = l0.clone(), m0.clone()
-        S.iterate(l, m, iters=iters)
+        ws, _ = S.iterate_checkpointed(l, m, iters=iters, ckpt_every=ck)
         gl, gM = S.lb_seed(l, m)
-        return S.backward(l0, m0, None, None, iters, ck, gl, gM)
+        return S.backward_checkpointed(None, None, iters, ck, gl, gM, ws)
     fwd_adj(A, lam0, M0)
     torch.cuda.synchronize()
     e0.record()
@@ -417,10 +417,11 @@ def run_ours(args):
             Mw.copy_(M0)
             torch.cuda.synchronize()
             ev[0].record(stream)
-            A.iterate(lamw, Mw, iters=T)
+            # forward keeping the checkpoints, loss seed, Alg. 2 from the checkpoints
+            A.iterate_checkpointed(lamw, Mw, iters=T, ckpt_every=ck, workspace=wsb)
             A.lb_seed_into(lamw, Mw, gl, gM)
             ev[1].record(stream)
-            A.backward_into(lam0, M0, None, None, T, ck, gl, gM, outs, wsb)
+            A.backward_checkpointed(None, None, T, ck, gl, gM, wsb, outs)
             ev[2].record(stream)
             torch.cuda.synchronize()
         f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])

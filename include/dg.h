@@ -253,6 +253,26 @@ dg_status dg_backward(dg_arena* arena, void* stream, const float* lam0, const fl
                       const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,
                       void* workspace, size_t ws_bytes, const dg_options* opts);
 
+/* dg_iterate(iters) on (lam, M) in place that also leaves in `workspace`
+ * (dg_backward_workspace_bytes(iters, ckpt_every) bytes) the checkpoints of
+ * (lam, M) dg_backward would otherwise recompute: the state at the start of
+ * every ckpt_every-iteration segment.  The final (lam, M) and lb_per_inst
+ * (optional, as in dg_iterate) are bit-identical to dg_iterate's.
+ * opts->renorm_every must be 0 (the adjoint does not differentiate the FP64
+ * re-projection): DG_EINVAL otherwise. */
+dg_status dg_iterate_checkpointed(dg_arena* arena, void* stream, float* lam, float* M, const float* omega,
+                                  const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every,
+                                  void* workspace, size_t ws_bytes, double* lb_per_inst, const dg_options* opts);
+
+/* dg_backward from the checkpoints a preceding dg_iterate_checkpointed left
+ * in `workspace` (same arena, iters, ckpt_every, omega, alpha, mode and
+ * options; the workspace untouched in between): skips the forward pass of
+ * dg_backward, results bit-identical to it. */
+dg_status dg_backward_checkpointed(dg_arena* arena, void* stream, const float* omega, const float* alpha,
+                                   int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
+                                   const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,
+                                   void* workspace, size_t ws_bytes, const dg_options* opts);
+
 /* --- DOGE-Train's updates around the solver ------------------------------ */
 
 /* Non-parametric update (eq. 2, Sec. 3.4):

@@ -77,6 +77,10 @@ SIGNATURES = {
     "dg_backward_workspace_bytes": (c_size_t, [P, c_int32, c_int32]),
     "dg_backward": (c_int32, [P, P, P, P, P, P, c_int32, c_int32, c_int32, P, P, P, P, P, P, P, c_size_t,
                               ctypes.POINTER(dg_options)]),
+    "dg_iterate_checkpointed": (c_int32, [P, P, P, P, P, P, c_int32, c_int32, c_int32, P, c_size_t, P,
+                                          ctypes.POINTER(dg_options)]),
+    "dg_backward_checkpointed": (c_int32, [P, P, P, P, c_int32, c_int32, c_int32, P, P, P, P, P, P, P, c_size_t,
+                                           ctypes.POINTER(dg_options)]),
     "dg_graph_create": (c_int32, [P, P, P, P, P, P, c_int32, c_int32, P, ctypes.POINTER(dg_options), PP]),
     "dg_graph_replay": (c_int32, [P, P]),
     "dg_graph_destroy": (None, [P]),

@@ -673,12 +673,18 @@ size_t dg_backward_workspace_bytes(const dg_arena* ar, int32_t iters, int32_t ck
   return backward_layout(ar, iters, ckpt_every).total;
 }
 
-dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float* M0, const float* omega,
-                      const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
-                      const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha, void* workspace,
-                      size_t ws_bytes, const dg_options* opts) {
+namespace {
+
+// dg_backward and dg_backward_checkpointed.  With lam0 == nullptr the
+// checkpoints are already in the workspace (dg_iterate_checkpointed) and the
+// forward pass is skipped.
+dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const float* M0, const float* omega,
+                        const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
+                        const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,
+                        void* workspace, size_t ws_bytes, const dg_options* opts) {
+  const bool have_ckpt = lam0 == nullptr;
   if (dg_status s = check_state(ar)) return s;
-  if (!lam0 || !M0 || !g_lam_T || !g_M_T || !g_lam0 || !g_M0 || !g_omega || !g_alpha)
+  if ((!have_ckpt && !M0) || !g_lam_T || !g_M_T || !g_lam0 || !g_M0 || !g_omega || !g_alpha)
     return fail(DG_EINVAL, "dg_backward: null pointer");
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_backward: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_backward: mode 1 needs omega and alpha");
@@ -727,9 +733,12 @@ dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float
   fa.omega0 = omega_of(opts);
   fa.mode = mode;
   // 1. forward pass keeping a checkpoint of (lambda, M) every k iterations
-  cpy(w_lam, lam0, bNS);
-  cpy(w_M, M0, bNS);
-  for (int c = 0; c < L.nseg; ++c) {
+  //    (already done by dg_iterate_checkpointed when have_ckpt)
+  if (!have_ckpt) {
+    cpy(w_lam, lam0, bNS);
+    cpy(w_M, M0, bNS);
+  }
+  for (int c = 0; c < (have_ckpt ? 0 : L.nseg); ++c) {
     cpy(ck_lam + (size_t)c * NS, w_lam, bNS);
     cpy(ck_M + (size_t)c * NS, w_M, bNS);
     if (c + 1 == L.nseg) break;
@@ -782,6 +791,59 @@ dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float
   launch_gather_var(A, sd_next, g_M0, st);
   if (e != cudaSuccess) return cuda_fail(e, "dg_backward copies");
   return check_launch("dg_backward");
+}
+
+}  // namespace
+
+dg_status dg_backward(dg_arena* ar, void* stream, const float* lam0, const float* M0, const float* omega,
+                      const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
+                      const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha, void* workspace,
+                      size_t ws_bytes, const dg_options* opts) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam0 || !M0) return fail(DG_EINVAL, "dg_backward: null pointer");
+  return backward_impl(ar, stream, lam0, M0, omega, alpha, mode, iters, ckpt_every, g_lam_T, g_M_T, g_lam0, g_M0,
+                       g_omega, g_alpha, workspace, ws_bytes, opts);
+}
+
+dg_status dg_backward_checkpointed(dg_arena* ar, void* stream, const float* omega, const float* alpha, int32_t mode,
+                                   int32_t iters, int32_t ckpt_every, const float* g_lam_T, const float* g_M_T,
+                                   float* g_lam0, float* g_M0, float* g_omega, float* g_alpha, void* workspace,
+                                   size_t ws_bytes, const dg_options* opts) {
+  return backward_impl(ar, stream, nullptr, nullptr, omega, alpha, mode, iters, ckpt_every, g_lam_T, g_M_T, g_lam0,
+                       g_M0, g_omega, g_alpha, workspace, ws_bytes, opts);
+}
+
+dg_status dg_iterate_checkpointed(dg_arena* ar, void* stream, float* lam, float* M, const float* omega,
+                                  const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every,
+                                  void* workspace, size_t ws_bytes, double* lb_out, const dg_options* opts) {
+  if (dg_status s = check_state(ar)) return s;
+  if (!lam || !M) return fail(DG_EINVAL, "dg_iterate_checkpointed: null state");
+  if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_iterate_checkpointed: mode must be 0 or 1");
+  if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_iterate_checkpointed: mode 1 needs omega and alpha");
+  if (iters < 0) return fail(DG_EINVAL, "dg_iterate_checkpointed: negative iteration count");
+  if (opts && opts->renorm_every > 0)
+    return fail(DG_EINVAL, "dg_iterate_checkpointed: the adjoint does not differentiate the FP64 re-projection "
+                           "(renorm_every must be 0)");
+  if (opts && opts->block_threads != 0 && (opts->block_threads % 32 != 0 || opts->block_threads > 512))
+    return fail(DG_EINVAL, "dg_iterate_checkpointed: block_threads must be a multiple of 32 in [32, 512]");
+  if (dg_status s = check_vectors("dg_iterate_checkpointed", lam, M, omega, alpha)) return s;
+  const BwdLayout L = backward_layout(ar, iters, ckpt_every);
+  if (iters > 0 && (!workspace || ws_bytes < L.total))
+    return fail(DG_EINVAL, "dg_iterate_checkpointed: workspace smaller than dg_backward_workspace_bytes()");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bNS = (size_t)ar->sizes.num_slots * 4;
+  char* w = (char*)workspace;
+  for (int c = 0; c < L.nseg; ++c) {
+    cudaError_t e = cudaMemcpyAsync(w + L.ck_lam + (size_t)c * bNS, lam, bNS, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w + L.ck_M + (size_t)c * bNS, M, bNS, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "dg_iterate_checkpointed copies");
+    const int k = std::min(L.k, iters - c * L.k);
+    const bool last = c + 1 == L.nseg;
+    if (dg_status s = enqueue_iterate(ar, st, lam, M, omega, alpha, mode, k, last ? lb_out : nullptr, opts))
+      return s;
+  }
+  if (iters == 0) return enqueue_iterate(ar, st, lam, M, omega, alpha, mode, 0, lb_out, opts);
+  return DG_OK;
 }
 
 }  // extern "C"

@@ -315,6 +315,37 @@ class Arena:
                                       ctypes.byref(self.options)), "dg_backward")
 
 
+    def iterate_checkpointed(self, lam, M, omega=None, alpha=None, iters=1, ckpt_every=10, workspace=None, lb=False,
+                             stream=None, **opt):
+        """``iterate`` in place that also keeps the checkpoints ``backward_checkpointed``
+        needs; returns (workspace, bound or None)."""
+        mode = 0 if omega is None else 1
+        if mode == 1 and alpha is None:
+            raise ValueError("per-slot omega needs per-slot alpha")
+        ws_bytes = self.backward_workspace_bytes(iters, ckpt_every)
+        if workspace is None:
+            workspace = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=self.device)
+        lb_out = torch.zeros(self.num_inst, dtype=torch.float64, device=self.device) if lb else None
+        o = self._opts(**opt)
+        check(_lib.load().dg_iterate_checkpointed(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(omega),
+                                                  _ptr(alpha), mode, int(iters), int(ckpt_every), _ptr(workspace),
+                                                  int(workspace.numel()), _ptr(lb_out), ctypes.byref(o)),
+              "dg_iterate_checkpointed")
+        return workspace, lb_out
+
+    def backward_checkpointed(self, omega, alpha, iters, ckpt_every, g_lamT, g_MT, workspace, outs=None,
+                              stream=None):
+        """Alg. 2 from the checkpoints of ``iterate_checkpointed``; returns
+        (g_lam0, g_M0, g_omega, g_alpha)."""
+        mode = 0 if omega is None else 1
+        outs = outs if outs is not None else [self.zeros() for _ in range(4)]
+        check(_lib.load().dg_backward_checkpointed(self._h, _stream_handle(stream), _ptr(omega), _ptr(alpha), mode,
+                                                   int(iters), int(ckpt_every), _ptr(g_lamT), _ptr(g_MT),
+                                                   *[_ptr(o) for o in outs], _ptr(workspace), int(workspace.numel()),
+                                                   ctypes.byref(self.options)), "dg_backward_checkpointed")
+        return tuple(outs)
+
+
 def wait(stream=None, timeout_ms=1000):
     """dg_wait: bounded host wait for the stream's work; returns the status."""
     return int(_lib.load().dg_wait(_stream_handle(stream), int(timeout_ms)))
@@ -322,8 +353,9 @@ def wait(stream=None, timeout_ms=1000):
 
 class DualIterate(torch.autograd.Function):
     """(lam0, M0, omega, alpha) -> (lam_T, M_T) through ``iters`` iterations of
-    Alg. 1 (dg_iterate); backward is Alg. 2 (dg_backward) with a checkpoint of
-    (lam, M) every ``ckpt_every`` iterations.  ``omega``/``alpha`` None selects
+    Alg. 1 (dg_iterate_checkpointed, which keeps (lam, M) every ``ckpt_every``
+    iterations); backward is Alg. 2 from those checkpoints
+    (dg_backward_checkpointed).  ``omega``/``alpha`` None selects
     the plain method (scalar omega of the arena's options, alpha = 1/|J_i|)."""
 
     @staticmethod
@@ -331,19 +363,21 @@ class DualIterate(torch.autograd.Function):
         lam, M = lam0.detach().clone(), M0.detach().clone()
         om = omega.detach() if omega is not None else None
         al = alpha.detach() if alpha is not None else None
-        arena.iterate(lam, M, om, al, iters=iters)
+        # the checkpoints of the backward pass are taken here, on the way
+        ctx.workspace, _ = arena.iterate_checkpointed(lam, M, om, al, iters=iters, ckpt_every=ckpt_every)
         ctx.arena, ctx.iters, ctx.ckpt = arena, int(iters), int(ckpt_every)
         ctx.has_params = omega is not None
-        ctx.save_for_backward(lam0.detach(), M0.detach(), om, al)
+        ctx.save_for_backward(om, al)
         return lam, M
 
     @staticmethod
     def backward(ctx, g_lam, g_M):
-        lam0, M0, om, al = ctx.saved_tensors
+        om, al = ctx.saved_tensors
         A = ctx.arena
         g_lam = A.zeros() if g_lam is None else g_lam.contiguous().float()
         g_M = A.zeros() if g_M is None else g_M.contiguous().float()
-        gl0, gM0, gw, ga = A.backward(lam0, M0, om, al, ctx.iters, ctx.ckpt, g_lam, g_M)
+        gl0, gM0, gw, ga = A.backward_checkpointed(om, al, ctx.iters, ctx.ckpt, g_lam, g_M, ctx.workspace)
+        ctx.workspace = None
         if not ctx.has_params:
             gw = ga = None
         return gl0, gM0, gw, ga, None, None, None

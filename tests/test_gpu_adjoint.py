@@ -147,3 +147,42 @@ def test_config3_matching_20_unrolled_iterations_lb_loss():
         rel = np.linalg.norm(g - w) / max(1e-12, np.linalg.norm(w))
         frac = np.mean(np.abs(g - w) <= 1e-4)
         assert rel < 1e-3 and frac >= 0.99, (rel, frac)
+
+
+@pytest.mark.parametrize("per_slot", [False, True])
+def test_checkpointed_forward_and_backward_are_bit_identical(per_slot):
+    """dg_iterate_checkpointed leaves (lam, M, bound) exactly as dg_iterate,
+    and dg_backward_checkpointed from its checkpoints gives exactly
+    dg_backward's gradients (the same kernels in the same order)."""
+    prob = workloads.matching_quadratic(L=40, R=40, pairs=1600, seed=9)
+    A = solver.plan(prob).bind()
+    lam0, M0 = A.init_lambda()
+    rng = np.random.default_rng(4)
+    om = al = None
+    if per_slot:
+        col = prob["col"]
+        z = np.exp(rng.normal(size=len(col)))
+        s = np.zeros(prob["n"])
+        np.add.at(s, col, z)
+        al = A.from_csr(z / s[col])
+        om = A.from_csr(1.0 / (1.0 + np.exp(-rng.normal(size=len(col)))))
+    T, ck = 7, 3
+    l1, m1 = lam0.clone(), M0.clone()
+    lb1 = A.iterate(l1, m1, om, al, iters=T, lb=True)
+    l2, m2 = lam0.clone(), M0.clone()
+    ws, lb2 = A.iterate_checkpointed(l2, m2, om, al, iters=T, ckpt_every=ck, lb=True)
+    assert torch.equal(l1, l2) and torch.equal(m1, m2) and torch.equal(lb1, lb2)
+    gl = A.from_csr(rng.normal(size=A.plan.sizes.num_lambda))
+    gM = A.from_csr(rng.normal(size=A.plan.sizes.num_lambda))
+    want = A.backward(lam0, M0, om, al, T, ck, gl, gM)
+    got = A.backward_checkpointed(om, al, T, ck, gl, gM, ws)
+    for x, y in zip(got, want):
+        assert torch.equal(x, y)
+
+
+def test_checkpointed_forward_rejects_renorm():
+    prob = workloads.matching_quadratic(L=20, R=20, pairs=200, seed=2)
+    A = solver.plan(prob, renorm_every=5).bind()
+    lam, M = A.init_lambda()
+    with pytest.raises(RuntimeError, match="re-projection"):
+        A.iterate_checkpointed(lam, M, iters=3, ckpt_every=2)

@@ -147,5 +147,9 @@ def test_calls_on_missing_arena_fail_cleanly():
     assert lib.dg_lower_bound(None, None, None, None, None, None) == _lib.DG_ESTATE
     assert lib.dg_backward(None, None, None, None, None, None, 0, 1, 1, None, None, None, None, None, None,
                            None, 0, None) == _lib.DG_ESTATE
+    assert lib.dg_iterate_checkpointed(None, None, None, None, None, None, 0, 1, 1, None, 0, None,
+                                       None) == _lib.DG_ESTATE
+    assert lib.dg_backward_checkpointed(None, None, None, None, 0, 1, 1, None, None, None, None, None, None,
+                                        None, 0, None) == _lib.DG_ESTATE
     assert lib.dg_graph_replay(None, None) == _lib.DG_EINVAL
     assert b"null" in lib.dg_last_error()
