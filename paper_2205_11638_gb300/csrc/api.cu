@@ -638,7 +638,8 @@ void dg_graph_destroy(dg_graph_t* g) {
 namespace {
 
 struct BwdLayout {
-  size_t ck_lam, ck_M, seg_lam, seg_S, w_lam, w_M, sdot, sd_a, sd_b, total;
+  size_t ck_lam, ck_M, rec_meta, rec_amin, rec_diff, seg_S, w_lam, w_M, sdot, sd_a, sd_b, total;
+  size_t meta_stride;  // bytes of one sweep's node records
   int nseg, k;
 };
 
@@ -655,7 +656,11 @@ BwdLayout backward_layout(const dg_arena* ar, int iters, int ckpt_every) {
   };
   L.ck_lam = put((size_t)L.nseg * NS * 4);
   L.ck_M = put((size_t)L.nseg * NS * 4);
-  L.seg_lam = put((size_t)2 * L.k * NS * 4);
+  // argmin records of every sweep of one segment (recording sweeps)
+  L.meta_stride = (size_t)ar->sizes.num_nodes_padded * 2;
+  L.rec_meta = put((size_t)2 * L.k * L.meta_stride);
+  L.rec_amin = put((size_t)2 * L.k * NS * 2);
+  L.rec_diff = put((size_t)2 * L.k * NS * 4);
   L.seg_S = put((size_t)2 * L.k * n * 4);
   L.w_lam = put(NS * 4);
   L.w_M = put(NS * 4);
@@ -695,6 +700,10 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   for (const AdjGroup& g : ar->adj_groups)
     if ((size_t)(mode ? g.region1 : g.region0) > ar->cta_smem_cap)
       return fail(DG_EINVAL, "dg_backward: a tile's adjoint state does not fit one CTA's shared memory");
+  for (const LaunchGroup& g : ar->groups)
+    if ((size_t)(mode ? g.region_bwd1 : g.region_bwd0) + (size_t)g.meta_bytes > ar->cta_smem_cap ||
+        (size_t)(mode ? g.region_bytes : g.region_bytes0) + (size_t)g.meta_bytes > ar->cta_smem_cap)
+      return fail(DG_EINVAL, "dg_backward: a tile's recording sweep does not fit one CTA's shared memory");
   const BwdLayout L = backward_layout(ar, iters, ckpt_every);
   if (iters > 0 && (!workspace || ws_bytes < L.total))
     return fail(DG_EINVAL, "dg_backward: workspace smaller than dg_backward_workspace_bytes()");
@@ -717,7 +726,9 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   char* w = (char*)workspace;
   float* ck_lam = (float*)(w + L.ck_lam);
   float* ck_M = (float*)(w + L.ck_M);
-  float* seg_lam = (float*)(w + L.seg_lam);
+  char* rec_meta = w + L.rec_meta;
+  uint16_t* rec_amin = (uint16_t*)(w + L.rec_amin);
+  float* rec_diff = (float*)(w + L.rec_diff);
   float* seg_S = (float*)(w + L.seg_S);
   float* w_lam = (float*)(w + L.w_lam);
   float* w_M = (float*)(w + L.w_M);
@@ -749,8 +760,9 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       launch_sweep(kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     }
   }
-  // 2. segments newest first: recompute, keeping lambda and S at every sweep
-  //    start, then run the adjoint sweeps backwards
+  // 2. segments newest first: recompute every sweep of the segment as a
+  //    recording sweep (its argmins and S at its start kept), then run the
+  //    adjoint sweeps backwards
   cpy(g_lam0, g_lam_T, bNS);
   AdjArgs aa{};
   aa.omega = omega;
@@ -768,16 +780,20 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
     cpy(w_lam, ck_lam + (size_t)c * NS, bNS);
     cpy(w_M, ck_M + (size_t)c * NS, bNS);
     for (int sw = 0; sw < nsw; ++sw) {
-      cpy(seg_lam + (size_t)sw * NS, w_lam, bNS);
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
       cpy(seg_S + (size_t)sw * n, A.S, bn);
-      if (sw + 1 < nsw)
-        launch_sweep(sw % 2 == 0 ? kFwd : kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(),
-                     streams_for(ar, st));
+      SweepArgs ra = fa;
+      ra.rec_meta = (uint16_t*)(rec_meta + (size_t)sw * L.meta_stride);
+      ra.rec_amin = rec_amin + (size_t)sw * NS;
+      ra.rec_diff = rec_diff + (size_t)sw * NS;
+      launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads, ar->groups.data(), (int)ar->groups.size(),
+                   streams_for(ar, st));
     }
     for (int sw = nsw - 1; sw >= 0; --sw) {
       const int gsw = 2 * it0 + sw;
-      aa.lam_old = seg_lam + (size_t)sw * NS;
+      aa.rec_meta = (const uint16_t*)(rec_meta + (size_t)sw * L.meta_stride);
+      aa.rec_amin = rec_amin + (size_t)sw * NS;
+      aa.rec_diff = rec_diff + (size_t)sw * NS;
       aa.S_in = seg_S + (size_t)sw * n;
       aa.seed_M = gsw == last_sweep ? g_M_T : nullptr;
       aa.sdot_next = gsw == last_sweep ? nullptr : sd_next;

@@ -387,6 +387,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
       for (int t = g.tile0; t < g.tile1; ++t) {
         g.region_bwd1 = std::max<int32_t>(g.region_bwd1, (int32_t)sweep_smem_bytes_bwd(P.tiles[t].nmax, P.tiles[t].nhops, 1));
         g.region_bwd0 = std::max<int32_t>(g.region_bwd0, (int32_t)sweep_smem_bytes_bwd(P.tiles[t].nmax, P.tiles[t].nhops, 0));
+        g.meta_bytes = std::max<int32_t>(g.meta_bytes, (P.tiles[t].nmax - 2) * kWarp * 2);
         smem_max = std::max<size_t>(smem_max, (size_t)g.region_bwd1);
       }
     // work estimate per group, then longest-processing-time assignment of the

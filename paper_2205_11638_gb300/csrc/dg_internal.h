@@ -95,6 +95,7 @@ struct LaunchGroup {
   int8_t wpc_fwd;         // tuned warps per CTA (0: choose by occupancy)
   int8_t wpc_bwd;
   int8_t pad[2];
+  int32_t meta_bytes;     // argmin records of the recording sweeps: 64 (nmax - 2), largest tile
 };
 
 // Tiles of one adjoint launch (the sweep's launch groups with the adjoint's
@@ -162,7 +163,7 @@ inline size_t sweep_smem_bytes_bwd(int nmax, int nhops, int mode) {
 // gradients, m1 - m0, a gather buffer and (mode 1) omega.
 inline size_t adjoint_smem_bytes(int nmax, int nhops, int mode) {
   const size_t nn = (size_t)nmax * kWarp, ns = (size_t)nhops * kWarp;
-  size_t b = nn * 10 + ns * (mode ? 36 : 32) + (size_t)(nmax - 2) * kWarp * 2;
+  size_t b = nn * 10 + ns * (mode ? 32 : 28) + (size_t)(nmax - 2) * kWarp * 2;
   return (b + 127) / 128 * 128;
 }
 

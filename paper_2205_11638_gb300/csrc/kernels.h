@@ -7,7 +7,9 @@
 
 namespace dg {
 
-enum SweepKind : int { kFwd = 0, kBwd = 1, kMinMarg = 2, kEnergy = 3, kSeed = 4 };
+// kFwdRec / kBwdRec: the update sweeps that also record, for the adjoint,
+// the argmins of their min-sum recursions (see SweepArgs::rec_*).
+enum SweepKind : int { kFwd = 0, kBwd = 1, kMinMarg = 2, kEnergy = 3, kSeed = 4, kFwdRec = 5, kBwdRec = 6 };
 
 struct SweepArgs {
   float* lam;          // in/out (read-only for kMinMarg/kEnergy/kSeed)
@@ -18,6 +20,10 @@ struct SweepArgs {
   float omega0;        // mode 0
   int mode;
   float* E;            // nullable: E^j per original row (kBwd, kEnergy)
+  // argmin records (kFwdRec, kBwdRec), read back by the adjoint of the sweep:
+  uint16_t* rec_meta;  // per node (layout of the child codes): in-arc parent | beta << 8 | hi-choice << 9
+  uint16_t* rec_amin;  // per slot: argmin node of m0 | argmin node of m1 << 8
+  float* rec_diff;     // per slot: m1 - m0
 };
 
 // The caller's stream plus kStreams - 1 auxiliary streams of an arena: the
@@ -57,7 +63,9 @@ void launch_seed_M(const DevArena& A, float* g_M, cudaStream_t st);
 
 // Backpropagation through one sweep (kernels_adjoint.cu).
 struct AdjArgs {
-  const float* lam_old;    // lambda at the start of the sweep (arena order)
+  const uint16_t* rec_meta;  // the records of the sweep (SweepArgs::rec_*)
+  const uint16_t* rec_amin;
+  const float* rec_diff;
   const float* S_in;       // S at the start of the sweep (per variable)
   const float* omega;      // mode 1
   const float* alpha;      // mode 1

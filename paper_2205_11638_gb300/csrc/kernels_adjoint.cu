@@ -3,12 +3,13 @@
 // formulation of App. B: gradients of min-marginals flow along the argmin
 // arcs of the min-sum recursions).
 //
-// One warp per tile, one lane per BDD, as in the forward sweeps.  A lane
-// first recomputes its sweep exactly as k_sweep does (same FP32 operations,
-// so the same values) and records, per node, the argmin in-arc of SP(r, .)
-// (smallest (parent rank, beta) on ties) and the argmin out-arc of SP(., T)
-// (0-arc on ties), and per level the argmin nodes of m0 and m1 (smallest
-// rank on ties).  It then runs the reverse of the sweep level by level:
+// One warp per tile, one lane per BDD, as in the forward sweeps.  The sweep
+// being differentiated was run as a recording sweep (k_sweep<kFwdRec/kBwdRec>
+// with the same FP32 operations as the plain sweep), which left per node the
+// argmin in-arc of SP(r, .) (smallest (parent rank, beta) on ties) and the
+// argmin out-arc of SP(., T) (0-arc on ties), and per level the argmin nodes
+// of m0 and m1 (smallest rank on ties) and m1 - m0.  A lane stages those
+// records and runs the reverse of the sweep level by level:
 //   lambda^new = lambda^old - M^new + alpha S^in,  M^new = omega (m1 - m0)
 // gives   S-dot contribution alpha * g, alpha-dot += g S^in,
 //         Mt = M-dot - g, omega-dot += Mt (m1 - m0),
@@ -26,20 +27,19 @@ namespace {
 
 // Shared-memory image of one tile in the adjoint kernels.
 struct AdjSmem {
-  float* a1;       // [32 * nmax] SP(., T), later its gradient
-  float* a2;       // [32 * nmax] SP(r, .), later its gradient
-  uint16_t* meta;  // [32 * nmax] parent node | beta << 8 | hi-choice << 9
+  float* a1;       // [32 * nmax] gradient of SP(., T)
+  float* a2;       // [32 * nmax] gradient of SP(r, .)
+  uint16_t* meta;  // [32 * nmax] parent node | beta << 8 | hi-choice << 9 (recorded)
   uint16_t* code;  // [32 * (nmax - 2)]
   uint16_t* desc;  // [32 * nh]
-  uint16_t* amin;  // [32 * nh] argmin node of m0 | argmin node of m1 << 8
-  float* lam;      // [32 * nh] lambda at sweep start
+  uint16_t* amin;  // [32 * nh] argmin node of m0 | argmin node of m1 << 8 (recorded)
   float* S;        // [32 * nh] S^in of the slot's variable
   float* al;       // [32 * nh] alpha
   float* om;       // [32 * nh] omega (mode 1)
   float* gl;       // [32 * nh] lambda gradient (new -> old)
   float* md;       // [32 * nh] gradient of M^new
-  float* diff;     // [32 * nh] m1 - m0
-  float* tmp;      // [32 * nh] variable ids, then gathered S-dot
+  float* diff;     // [32 * nh] m1 - m0 (recorded)
+  float* tmp;      // [32 * nh] variable ids, then gathered S-dot, then S-dot contributions
   int nmax, nh;
 };
 
@@ -57,8 +57,6 @@ __device__ __forceinline__ AdjSmem carve_adj(unsigned char* p, const Tile& T) {
   p += (size_t)nn * 4;
   s.a2 = (float*)p;
   p += (size_t)nn * 4;
-  s.lam = (float*)p;
-  p += (size_t)ns * 4;
   s.S = (float*)p;
   p += (size_t)ns * 4;
   s.al = (float*)p;
@@ -100,10 +98,12 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   const int ns = s.nh * kWarp;
   const int64_t sb = T.slot_base;
 
-  // ---- staging ----------------------------------------------------------
+  // ---- staging: the sweep's records, the gradients, the S^in gathers ----
   copy_async(s.code + 2 * kWarp, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+  copy_async(s.meta + 2 * kWarp, a.rec_meta + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
   copy_async(s.desc, A.desc + sb, ns * 2, lane);
-  copy_async(s.lam, a.lam_old + sb, ns * 4, lane);
+  copy_async(s.amin, a.rec_amin + sb, ns * 2, lane);
+  copy_async(s.diff, a.rec_diff + sb, ns * 4, lane);
   copy_async(s.gl, a.g_lam + sb, ns * 4, lane);
   copy_async(s.tmp, A.slot_var + sb, ns * 4, lane);
   if (MODE == 1) {
@@ -112,8 +112,11 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   }
   if (a.seed_M) copy_async(s.md, a.seed_M + sb, ns * 4, lane);
   cp_async_commit();
-  A1(kTopCode) = 0.0f;
-  A1(kBotCode) = f_inf();
+  // gradient accumulators of SP(., T) and SP(r, .)
+  for (int n = 0; n < s.nmax; ++n) {
+    A1(n) = 0.0f;
+    A2(n) = 0.0f;
+  }
   cp_async_wait_all();
   __syncwarp();
   {
@@ -137,140 +140,11 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
     }
     cp_async_commit();
   }
-
-  // ---- forward recompute with argmin records ----------------------------
-  if (FWD) {
-    // SP(., T) bottom-up under lambda^old; hi-choice bit per node
-    for (int h = s.nh - 1; h >= 0; --h) {
-      const uint32_t ds = s.desc[h * kWarp + lane];
-      const int w = desc_width(ds);
-      if (w == 0) continue;
-      const int fn = desc_first(ds);
-      const float l = s.lam[h * kWarp + lane];
-      for (int r = 0; r < w; ++r) {
-        const int n = fn + r;
-        const uint32_t c = node_code(s.code, n, lane);
-        const float tl = A1(c & 0xFFu), th = l + A1(c >> 8);
-        const bool take0 = (c & 0xFFu) != kBotCode && tl <= th;
-        A1(n) = take0 ? tl : th;
-        META(n) = take0 ? 0 : (1u << 9);
-      }
-    }
-  } else {
-    // SP(r, .) top-down under lambda^old; argmin in-arc per node
-    if (desc_width(s.desc[lane]) > 0) A2(2) = 0.0f;
-    for (int h = 0; h + 1 < s.nh; ++h) {
-      const uint32_t ds = s.desc[h * kWarp + lane], dn = s.desc[(h + 1) * kWarp + lane];
-      const int w = desc_width(ds), wn = desc_width(dn);
-      if (wn == 0) break;
-      const int fn = desc_first(ds), fnn = desc_first(dn);
-      const float l = s.lam[h * kWarp + lane];
-      for (int r = 0; r < wn; ++r) A2(fnn + r) = f_inf();
-      for (int r = 0; r < w; ++r) {
-        const int n = fn + r;
-        const uint32_t c = node_code(s.code, n, lane);
-        const uint32_t lo = c & 0xFFu, hi = c >> 8;
-        const float dv = A2(n);
-        if (lo >= 2 && dv < A2(lo)) {
-          A2(lo) = dv;
-          META(lo) = (uint16_t)n;
-        }
-        if (hi >= 2 && dv + l < A2(hi)) {
-          A2(hi) = dv + l;
-          META(hi) = (uint16_t)(n | (1u << 8));
-        }
-      }
-    }
-  }
   wait_gathers();
   for (int q = lane; q < ns; q += kWarp) s.md[q] += s.tmp[q];  // gradient of M^new
   __syncwarp();
 
-  if (FWD) {
-    if (desc_width(s.desc[lane]) > 0) A2(2) = 0.0f;
-    for (int h = 0; h < s.nh; ++h) {
-      const uint32_t ds = s.desc[h * kWarp + lane];
-      const int w = desc_width(ds);
-      if (w == 0) break;
-      const int fn = desc_first(ds);
-      const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
-      const int wn = desc_width(dn), fnn = desc_first(dn);
-      float b0 = f_inf(), b1 = f_inf();
-      int v0 = fn, v1 = fn;
-      for (int r = 0; r < w; ++r) {
-        const int n = fn + r;
-        const uint32_t c = node_code(s.code, n, lane);
-        const float dv = A2(n);
-        const float x0 = dv + A1(c & 0xFFu), x1 = dv + A1(c >> 8);
-        if (x0 < b0) { b0 = x0; v0 = n; }
-        if (x1 < b1) { b1 = x1; v1 = n; }
-      }
-      const int q = h * kWarp + lane;
-      const float l = s.lam[q];
-      const float m0 = b0, m1 = l + b1;
-      const float om = MODE == 1 ? s.om[q] : a.omega0;
-      const float Mn = om * (m1 - m0);
-      const float ln = l - Mn + s.al[q] * s.S[q];
-      s.diff[q] = m1 - m0;
-      s.amin[q] = (uint16_t)(v0 | (v1 << 8));
-      if (wn > 0) {
-        for (int r = 0; r < wn; ++r) A2(fnn + r) = f_inf();
-        for (int r = 0; r < w; ++r) {
-          const int n = fn + r;
-          const uint32_t c = node_code(s.code, n, lane);
-          const uint32_t lo = c & 0xFFu, hi = c >> 8;
-          const float dv = A2(n);
-          if (lo >= 2 && dv < A2(lo)) {
-            A2(lo) = dv;
-            META(lo) = (uint16_t)((META(lo) & (1u << 9)) | n);
-          }
-          if (hi >= 2 && dv + ln < A2(hi)) {
-            A2(hi) = dv + ln;
-            META(hi) = (uint16_t)((META(hi) & (1u << 9)) | n | (1u << 8));
-          }
-        }
-      }
-    }
-  } else {
-    for (int h = s.nh - 1; h >= 0; --h) {
-      const uint32_t ds = s.desc[h * kWarp + lane];
-      const int w = desc_width(ds);
-      if (w == 0) continue;
-      const int fn = desc_first(ds);
-      float b0 = f_inf(), b1 = f_inf();
-      int v0 = fn, v1 = fn;
-      for (int r = 0; r < w; ++r) {
-        const int n = fn + r;
-        const uint32_t c = node_code(s.code, n, lane);
-        const float dv = A2(n);
-        const float x0 = dv + A1(c & 0xFFu), x1 = dv + A1(c >> 8);
-        if (x0 < b0) { b0 = x0; v0 = n; }
-        if (x1 < b1) { b1 = x1; v1 = n; }
-      }
-      const int q = h * kWarp + lane;
-      const float l = s.lam[q];
-      const float m0 = b0, m1 = l + b1;
-      const float om = MODE == 1 ? s.om[q] : a.omega0;
-      const float Mn = om * (m1 - m0);
-      const float ln = l - Mn + s.al[q] * s.S[q];
-      s.diff[q] = m1 - m0;
-      s.amin[q] = (uint16_t)(v0 | (v1 << 8));
-      for (int r = 0; r < w; ++r) {
-        const int n = fn + r;
-        const uint32_t c = node_code(s.code, n, lane);
-        const float tl = A1(c & 0xFFu), th = ln + A1(c >> 8);
-        const bool take0 = (c & 0xFFu) != kBotCode && tl <= th;
-        A1(n) = take0 ? tl : th;
-        META(n) = (uint16_t)((META(n) & 0x1FFu) | (take0 ? 0u : (1u << 9)));
-      }
-    }
-  }
-
   // ---- reverse ------------------------------------------------------------
-  for (int n = 0; n < s.nmax; ++n) {
-    A1(n) = 0.0f;  // gradient of SP(., T)
-    A2(n) = 0.0f;  // gradient of SP(r, .)
-  }
   // one step of the reverse: the update and the min-marginal argmins of level h
   auto reverse_level = [&](int h) {
     const int q = h * kWarp + lane;

@@ -22,19 +22,28 @@ static size_t g_cta_smem_cap = 227 * 1024;
 
 template <int KIND, int MODE>
 __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int region_bytes, int tile0, int tile1) {
+  // kFwdRec / kBwdRec are kFwd / kBwd that also record the argmins of their
+  // recursions for the adjoint: strict comparisons in node order instead of
+  // fminf (the same values, plus the winner), and the records written out
+  constexpr bool REC = KIND == kFwdRec || KIND == kBwdRec;
+  constexpr bool FWD = KIND == kFwd || KIND == kFwdRec;
+  constexpr bool BWD = KIND == kBwd || KIND == kBwdRec;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tile = tile0 + blockIdx.x * (blockDim.x >> 5) + warp;
   if (tile >= tile1) return;  // whole warp leaves; no CTA-wide barrier follows
   const Tile T = A.tiles[tile];
-  TileSmem s = carve<MODE, KIND != kBwd>(smem + (size_t)warp * region_bytes, T);
-  load_tile<KIND == kFwd || KIND == kBwd, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane);
+  TileSmem s = carve<MODE, !BWD, REC>(smem + (size_t)warp * region_bytes, T);
+  load_tile<FWD || BWD, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane);
   const int64_t sbase = T.slot_base;
 
-  if (KIND == kFwd || KIND == kMinMarg) {
+  if (FWD || KIND == kMinMarg) {
     // ---- SP(., T) under lambda at sweep start, then the forward sweep -----
-    lane_cost_to_top(s, lane);
-    if (KIND == kFwd) wait_gathers();
+    if (REC)
+      lane_cost_to_top_rec(s, lane);
+    else
+      lane_cost_to_top(s, lane);
+    if (FWD) wait_gathers();
     if (desc_width(s.desc[lane]) > 0) DG_R(s, 2) = 0.0f;
     for (int h = 0; h < s.nh; ++h) {
       const uint32_t ds = s.desc[h * kWarp + lane];
@@ -44,13 +53,20 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
       const int wn = desc_width(dn), fnn = desc_first(dn);
       float b0 = f_inf(), b1 = f_inf();
+      int v0 = fn, v1 = fn;
       #pragma unroll 2
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
         const float dv = DG_R(s, n);
-        b0 = fminf(b0, dv + DG_F(s, c & 0xFFu));
-        b1 = fminf(b1, dv + DG_F(s, c >> 8));
+        const float x0 = dv + DG_F(s, c & 0xFFu), x1 = dv + DG_F(s, c >> 8);
+        if (REC) {
+          if (x0 < b0) { b0 = x0; v0 = n; }
+          if (x1 < b1) { b1 = x1; v1 = n; }
+        } else {
+          b0 = fminf(b0, x0);
+          b1 = fminf(b1, x1);
+        }
       }
       const int q = h * kWarp + lane;
       const float l = s.lam[q];
@@ -65,6 +81,10 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         ln = l - Mn + slot_avg<MODE>(s, q);
         a.lam[sbase + q] = ln;
         a.M[sbase + q] = Mn;
+        if (REC) {
+          a.rec_amin[sbase + q] = (uint16_t)(v0 | (v1 << 8));
+          a.rec_diff[sbase + q] = m1 - m0;
+        }
       }
       if (wn > 0) {
         #pragma unroll 2
@@ -75,14 +95,28 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
           const uint32_t c = node_code(s, n, lane);
           const uint32_t lo = c & 0xFFu, hi = c >> 8;
           const float dv = DG_R(s, n);
-          if (lo != kBotCode) DG_R(s, lo) = fminf(DG_R(s, lo), dv);
-          if (hi != kBotCode) DG_R(s, hi) = fminf(DG_R(s, hi), dv + ln);
+          if (REC) {
+            if (lo >= 2 && dv < DG_R(s, lo)) {
+              DG_R(s, lo) = dv;
+              DG_META(s, lo) = (uint16_t)((DG_META(s, lo) & kHiChoice) | n);
+            }
+            if (hi >= 2 && dv + ln < DG_R(s, hi)) {
+              DG_R(s, hi) = dv + ln;
+              DG_META(s, hi) = (uint16_t)((DG_META(s, hi) & kHiChoice) | n | kInHi);
+            }
+          } else {
+            if (lo != kBotCode) DG_R(s, lo) = fminf(DG_R(s, lo), dv);
+            if (hi != kBotCode) DG_R(s, hi) = fminf(DG_R(s, hi), dv + ln);
+          }
         }
       }
     }
-  } else if (KIND == kBwd) {
+  } else if (BWD) {
     // ---- SP(r, .) under lambda at sweep start, then the backward sweep ----
-    lane_cost_from_root(s, lane);
+    if (REC)
+      lane_cost_from_root_rec(s, lane);
+    else
+      lane_cost_from_root(s, lane);
     wait_gathers();
     DG_W(s, kTopCode) = 0.0f;
     DG_W(s, kBotCode) = f_inf();
@@ -92,13 +126,20 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       if (w == 0) continue;
       const int fn = desc_first(ds);
       float b0 = f_inf(), b1 = f_inf();
+      int v0 = fn, v1 = fn;
       #pragma unroll 2
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
         const float dv = DG_F(s, n);
-        b0 = fminf(b0, dv + DG_W(s, c & 0xFFu));
-        b1 = fminf(b1, dv + DG_W(s, c >> 8));
+        const float x0 = dv + DG_W(s, c & 0xFFu), x1 = dv + DG_W(s, c >> 8);
+        if (REC) {
+          if (x0 < b0) { b0 = x0; v0 = n; }
+          if (x1 < b1) { b1 = x1; v1 = n; }
+        } else {
+          b0 = fminf(b0, x0);
+          b1 = fminf(b1, x1);
+        }
       }
       const int q = h * kWarp + lane;
       const float l = s.lam[q];
@@ -108,11 +149,22 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const float ln = l - Mn + slot_avg<MODE>(s, q);
       a.lam[sbase + q] = ln;
       a.M[sbase + q] = Mn;
+      if (REC) {
+        a.rec_amin[sbase + q] = (uint16_t)(v0 | (v1 << 8));
+        a.rec_diff[sbase + q] = m1 - m0;
+      }
       #pragma unroll 2
       for (int r = 0; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
-        DG_W(s, n) = fminf(DG_W(s, c & 0xFFu), ln + DG_W(s, c >> 8));
+        if (REC) {
+          const float tl = DG_W(s, c & 0xFFu), th = ln + DG_W(s, c >> 8);
+          const bool take0 = (c & 0xFFu) != kBotCode && tl <= th;
+          DG_W(s, n) = take0 ? tl : th;
+          DG_META(s, n) = (uint16_t)((DG_META(s, n) & 0x1FFu) | (take0 ? 0u : kHiChoice));
+        } else {
+          DG_W(s, n) = fminf(DG_W(s, c & 0xFFu), ln + DG_W(s, c >> 8));
+        }
       }
     }
   } else {
@@ -132,6 +184,14 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       a.M[sbase + q] = take0 ? 0.f : 1.f;
       n = (int)(take0 ? lo : hi);
     }
+  }
+
+  if (REC) {
+    // the records of nodes 2 .. nmax-1, in the layout of the child codes
+    __syncwarp();
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(s.meta + 2 * kWarp);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(a.rec_meta + T.node_base);
+    for (int o = lane; o < (s.nmax - 2) * (kWarp / 2); o += kWarp) dst[o] = src[o];
   }
 
   if ((KIND == kBwd || KIND == kEnergy) && a.E != nullptr && lane < T.nbdd) {
@@ -238,6 +298,8 @@ cudaError_t set_sweep_smem_limit(size_t bytes) {
   if (e == cudaSuccess) e = set_attr<kMinMarg>(b);
   if (e == cudaSuccess) e = set_attr<kEnergy>(b);
   if (e == cudaSuccess) e = set_attr<kSeed>(b);
+  if (e == cudaSuccess) e = set_attr<kFwdRec>(b);
+  if (e == cudaSuccess) e = set_attr<kBwdRec>(b);
   return e;
 }
 
@@ -285,11 +347,14 @@ static void launch_groups(const DevArena& A, const SweepArgs& a, int threads, co
   if (fork) ss.begin();
   for (int g = 0; g < num_groups; ++g) {
     const LaunchGroup& G = groups[g];
-    const size_t region = (size_t)(KIND == kBwd ? (MODE == 1 ? G.region_bwd1 : G.region_bwd0)
-                                                : (MODE == 1 ? G.region_bytes : G.region_bytes0));
+    constexpr bool REC = KIND == kFwdRec || KIND == kBwdRec;
+    constexpr bool BWD = KIND == kBwd || KIND == kBwdRec;
+    const size_t region = (size_t)(BWD ? (MODE == 1 ? G.region_bwd1 : G.region_bwd0)
+                                       : (MODE == 1 ? G.region_bytes : G.region_bytes0)) +
+                          (REC ? (size_t)G.meta_bytes : 0);
     int wpc = threads / kWarp;
     if (wpc > 4) wpc = 4;  // __launch_bounds__(128)
-    const int tuned = KIND == kBwd ? G.wpc_bwd : G.wpc_fwd;
+    const int tuned = REC ? 0 : (BWD ? G.wpc_bwd : G.wpc_fwd);
     if (tuned > 0 && region * tuned <= g_cta_smem_cap)
       wpc = tuned;
     else
@@ -316,6 +381,14 @@ void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, 
     case kBwd:
       m1 ? launch_groups<kBwd, 1>(A, a, threads, groups, num_groups, st)
          : launch_groups<kBwd, 0>(A, a, threads, groups, num_groups, st);
+      break;
+    case kFwdRec:
+      m1 ? launch_groups<kFwdRec, 1>(A, a, threads, groups, num_groups, st)
+         : launch_groups<kFwdRec, 0>(A, a, threads, groups, num_groups, st);
+      break;
+    case kBwdRec:
+      m1 ? launch_groups<kBwdRec, 1>(A, a, threads, groups, num_groups, st)
+         : launch_groups<kBwdRec, 0>(A, a, threads, groups, num_groups, st);
       break;
     case kMinMarg: launch_groups<kMinMarg, 0>(A, a, threads, groups, num_groups, st); break;
     case kEnergy: launch_groups<kEnergy, 0>(A, a, threads, groups, num_groups, st); break;

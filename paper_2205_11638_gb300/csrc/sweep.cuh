@@ -34,12 +34,14 @@ struct TileSmem {
   uint16_t* desc;  // [32 * nh]
   uint16_t* code;       // child codes, biased: element 32 n + lane is node number n
   uint16_t* code_base;  // [32 * (nmax - 2)] the staged codes of nodes 2 .. nmax-1
+  uint16_t* meta;       // recording sweeps: argmin record per node, biased like code
   int nmax, nh, rmask;
 };
 
 // RING: the sweep-direction costs live in a ring of T.ring node numbers;
 // otherwise in a second whole array (s.ring then indexed by node number).
-template <int MODE, bool RING>
+// REC: an argmin record per node follows the child codes.
+template <int MODE, bool RING, bool REC = false>
 __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
   TileSmem s;
   s.nmax = T.nmax;
@@ -66,8 +68,14 @@ __device__ __forceinline__ TileSmem carve(unsigned char* p, const Tile& T) {
   p += (size_t)ns * 2;
   s.code_base = (uint16_t*)p;
   s.code = s.code_base - 2 * kWarp;
+  s.meta = REC ? s.code + (size_t)(s.nmax - 2) * kWarp : nullptr;
   return s;
 }
+
+// Argmin record of node number n >= 2 (recording sweeps).
+#define DG_META(s, n) (s).meta[(n) * kWarp + lane]
+constexpr uint32_t kHiChoice = 1u << 9;  // SP(v, top) leaves v by its 1-arc
+constexpr uint32_t kInHi = 1u << 8;      // SP(root, v) enters v by a 1-arc
 
 // Cost arrays of lane `lane`: DG_F is the element of node number n in the
 // first-pass array (numbers 0 and 1 hold the terminal costs 0 and +inf);
@@ -194,6 +202,27 @@ __device__ __forceinline__ void lane_cost_to_top(TileSmem& s, int lane) {
   }
 }
 
+// lane_cost_to_top that also records per node whether the minimum leaves by
+// the 1-arc (kHiChoice; the 0-arc wins ties), the rest of the record cleared.
+__device__ __forceinline__ void lane_cost_to_top_rec(TileSmem& s, int lane) {
+  for (int h = s.nh - 1; h >= 0; --h) {
+    const uint32_t ds = s.desc[h * kWarp + lane];
+    const int w = desc_width(ds);
+    if (w == 0) continue;
+    const int fn = desc_first(ds);
+    const float l = s.lam[h * kWarp + lane];
+    #pragma unroll 2
+    for (int r = 0; r < w; ++r) {
+      const int n = fn + r;
+      const uint32_t c = node_code(s, n, lane);
+      const float tl = DG_F(s, c & 0xFFu), th = l + DG_F(s, c >> 8);
+      const bool take0 = (c & 0xFFu) != kBotCode && tl <= th;
+      DG_F(s, n) = take0 ? tl : th;
+      DG_META(s, n) = take0 ? 0 : kHiChoice;
+    }
+  }
+}
+
 // SP(root, v) of every node of my BDD under s.lam into s.full (levels
 // top-down).
 __device__ __forceinline__ void lane_cost_from_root(TileSmem& s, int lane) {
@@ -217,6 +246,40 @@ __device__ __forceinline__ void lane_cost_from_root(TileSmem& s, int lane) {
       // arcs into the bottom terminal write its entry, which this pass never reads
       DG_F(s, lo) = fminf(DG_F(s, lo), dv);
       DG_F(s, hi) = fminf(DG_F(s, hi), dv + l);
+    }
+  }
+}
+
+// lane_cost_from_root that also records per node its argmin in-arc: the
+// parent's node number | kInHi for a 1-arc; the first strictly smaller
+// candidate wins (parents in node order, the 0-arc before the 1-arc).
+__device__ __forceinline__ void lane_cost_from_root_rec(TileSmem& s, int lane) {
+  if (desc_width(s.desc[lane]) == 0) return;
+  DG_F(s, 2) = 0.0f;
+  DG_META(s, 2) = 0;
+  for (int h = 0; h + 1 < s.nh; ++h) {
+    const uint32_t ds = s.desc[h * kWarp + lane];
+    const uint32_t dn = s.desc[(h + 1) * kWarp + lane];
+    const int w = desc_width(ds), wn = desc_width(dn);
+    if (wn == 0) break;
+    const int fn = desc_first(ds), fnn = desc_first(dn);
+    const float l = s.lam[h * kWarp + lane];
+    #pragma unroll 2
+    for (int r = 0; r < wn; ++r) DG_F(s, fnn + r) = f_inf();
+    #pragma unroll 2
+    for (int r = 0; r < w; ++r) {
+      const int n = fn + r;
+      const uint32_t c = node_code(s, n, lane);
+      const uint32_t lo = c & 0xFFu, hi = c >> 8;
+      const float dv = DG_F(s, n);
+      if (lo >= 2 && dv < DG_F(s, lo)) {
+        DG_F(s, lo) = dv;
+        DG_META(s, lo) = (uint16_t)n;
+      }
+      if (hi >= 2 && dv + l < DG_F(s, hi)) {
+        DG_F(s, hi) = dv + l;
+        DG_META(s, hi) = (uint16_t)(n | kInHi);
+      }
     }
   }
 }
