@@ -20,6 +20,12 @@ namespace dg {
 
 static size_t g_cta_smem_cap = 227 * 1024;
 
+// Nodes of a level whose child costs the backward sweeps keep in registers
+// between the level's two passes (most levels are this narrow).  The forward
+// sweeps measured faster without such a cache (register pressure).
+constexpr int kCacheFwd = 0;
+constexpr int kCacheBwd = 4;
+
 template <int KIND, int MODE>
 __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int region_bytes, int tile0, int tile1) {
   // kFwdRec / kBwdRec are kFwd / kBwd that also record the argmins of their
@@ -54,8 +60,24 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const int wn = desc_width(dn), fnn = desc_first(dn);
       float b0 = f_inf(), b1 = f_inf();
       int v0 = fn, v1 = fn;
+      // the codes and costs of the level's first kCacheFwd nodes stay in
+      // registers for the relaxation below
+      constexpr int CF = REC ? 0 : kCacheFwd;
+      uint32_t cc[CF > 0 ? CF : 1];
+      float dd[CF > 0 ? CF : 1];
+      #pragma unroll
+      for (int i = 0; i < CF; ++i) {
+        cc[i] = 0u;
+        dd[i] = 0.0f;
+        if (i < w) {
+          cc[i] = node_code(s, fn + i, lane);
+          dd[i] = DG_R(s, fn + i);
+          b0 = fminf(b0, dd[i] + DG_F(s, cc[i] & 0xFFu));
+          b1 = fminf(b1, dd[i] + DG_F(s, cc[i] >> 8));
+        }
+      }
       #pragma unroll 2
-      for (int r = 0; r < w; ++r) {
+      for (int r = CF; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
         const float dv = DG_R(s, n);
@@ -89,8 +111,16 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       if (wn > 0) {
         #pragma unroll 2
         for (int r = 0; r < wn; ++r) DG_R(s, fnn + r) = f_inf();
+        #pragma unroll
+        for (int i = 0; i < CF; ++i) {
+          if (i < w) {
+            const uint32_t lo = cc[i] & 0xFFu, hi = cc[i] >> 8;
+            if (lo != kBotCode) DG_R(s, lo) = fminf(DG_R(s, lo), dd[i]);
+            if (hi != kBotCode) DG_R(s, hi) = fminf(DG_R(s, hi), dd[i] + ln);
+          }
+        }
         #pragma unroll 2
-        for (int r = 0; r < w; ++r) {
+        for (int r = CF; r < w; ++r) {
           const int n = fn + r;
           const uint32_t c = node_code(s, n, lane);
           const uint32_t lo = c & 0xFFu, hi = c >> 8;
@@ -127,8 +157,24 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       const int fn = desc_first(ds);
       float b0 = f_inf(), b1 = f_inf();
       int v0 = fn, v1 = fn;
+      // the child costs of the level's first kCacheBwd nodes stay in registers
+      // for the level's own costs below
+      constexpr int CB = REC ? 0 : kCacheBwd;
+      float wl[CB > 0 ? CB : 1], wh[CB > 0 ? CB : 1];
+      #pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        wl[i] = wh[i] = 0.0f;
+        if (i < w) {
+          const uint32_t c = node_code(s, fn + i, lane);
+          const float dv = DG_F(s, fn + i);
+          wl[i] = DG_W(s, c & 0xFFu);
+          wh[i] = DG_W(s, c >> 8);
+          b0 = fminf(b0, dv + wl[i]);
+          b1 = fminf(b1, dv + wh[i]);
+        }
+      }
       #pragma unroll 2
-      for (int r = 0; r < w; ++r) {
+      for (int r = CB; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
         const float dv = DG_F(s, n);
@@ -153,8 +199,11 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         a.rec_amin[sbase + q] = (uint16_t)(v0 | (v1 << 8));
         a.rec_diff[sbase + q] = m1 - m0;
       }
+      #pragma unroll
+      for (int i = 0; i < CB; ++i)
+        if (i < w) DG_W(s, fn + i) = fminf(wl[i], ln + wh[i]);
       #pragma unroll 2
-      for (int r = 0; r < w; ++r) {
+      for (int r = CB; r < w; ++r) {
         const int n = fn + r;
         const uint32_t c = node_code(s, n, lane);
         if (REC) {
