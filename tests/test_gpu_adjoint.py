@@ -186,3 +186,27 @@ def test_checkpointed_forward_rejects_renorm():
     lam, M = A.init_lambda()
     with pytest.raises(RuntimeError, match="re-projection"):
         A.iterate_checkpointed(lam, M, iters=3, ckpt_every=2)
+
+
+@pytest.mark.parametrize("T,ck", [(0, 3), (2, 50), (5, 1)])
+def test_checkpointed_edge_intervals(T, ck):
+    """No iterations (gradients pass through, bound of the initial state), a
+    checkpoint interval longer than the unroll, and one checkpoint per
+    iteration: the checkpointed pair still equals dg_iterate + dg_backward."""
+    prob = workloads.matching_quadratic(L=30, R=30, pairs=900, seed=12)
+    A = solver.plan(prob).bind()
+    lam0, M0 = A.init_lambda()
+    l1, m1 = lam0.clone(), M0.clone()
+    lb1 = A.iterate(l1, m1, iters=T, lb=True)
+    l2, m2 = lam0.clone(), M0.clone()
+    ws, lb2 = A.iterate_checkpointed(l2, m2, iters=T, ckpt_every=ck, lb=True)
+    assert torch.equal(l1, l2) and torch.equal(m1, m2) and torch.equal(lb1, lb2)
+    rng = np.random.default_rng(T + 10 * ck)
+    gl = A.from_csr(rng.normal(size=A.plan.sizes.num_lambda))
+    gM = A.from_csr(rng.normal(size=A.plan.sizes.num_lambda))
+    want = A.backward(lam0, M0, None, None, T, ck, gl, gM)
+    got = A.backward_checkpointed(None, None, T, ck, gl, gM, ws)
+    for x, y in zip(got, want):
+        assert torch.equal(x, y)
+    if T == 0:
+        assert torch.equal(got[0], gl) and torch.equal(got[1], gM)
