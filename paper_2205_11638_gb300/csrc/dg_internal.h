@@ -157,13 +157,14 @@ inline size_t sweep_smem_bytes(int nmax, int nhops, int mode, int ring) {
 inline size_t sweep_smem_bytes_bwd(int nmax, int nhops, int mode) {
   return sweep_smem_bytes(nmax, nhops, mode, nmax);
 }
-// ... and in the adjoint kernels: two cost arrays (reused for their
-// gradients), an argmin record and the child codes per node; per slot the
-// descriptor, the argmin nodes of m0/m1, lambda, S, alpha, the lambda and M
-// gradients, m1 - m0, a gather buffer and (mode 1) omega.
+// ... and in the adjoint kernels: two gradient arrays, the argmin record and
+// the child codes per node; per slot the descriptor, the lambda gradient and
+// the variable (the other per-slot inputs of the reverse are read into
+// registers a level ahead, the same in both modes).
 inline size_t adjoint_smem_bytes(int nmax, int nhops, int mode) {
   const size_t nn = (size_t)nmax * kWarp, ns = (size_t)nhops * kWarp;
-  size_t b = nn * 10 + ns * (mode ? 32 : 28) + (size_t)(nmax - 2) * kWarp * 2;
+  size_t b = nn * 10 + ns * 10 + (size_t)(nmax - 2) * kWarp * 2;
+  (void)mode;
   return (b + 127) / 128 * 128;
 }
 

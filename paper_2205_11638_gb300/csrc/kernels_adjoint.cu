@@ -25,21 +25,20 @@ namespace dg {
 
 namespace {
 
-// Shared-memory image of one tile in the adjoint kernels.
+// Shared-memory image of one tile in the adjoint kernels: what the level
+// loops walk node by node.  The per-slot inputs of the update's reverse
+// (S^in, alpha, omega, M-dot, the recorded argmins and m1 - m0, and the
+// running omega-dot / alpha-dot sums) are read from global memory into
+// registers one level ahead instead (see LevelIn), which keeps a tile's
+// footprint small enough for more warps per SM.
 struct AdjSmem {
   float* a1;       // [32 * nmax] gradient of SP(., T)
   float* a2;       // [32 * nmax] gradient of SP(r, .)
   uint16_t* meta;  // [32 * nmax] parent node | beta << 8 | hi-choice << 9 (recorded)
   uint16_t* code;  // [32 * (nmax - 2)]
   uint16_t* desc;  // [32 * nh]
-  uint16_t* amin;  // [32 * nh] argmin node of m0 | argmin node of m1 << 8 (recorded)
-  float* S;        // [32 * nh] S^in of the slot's variable
-  float* al;       // [32 * nh] alpha
-  float* om;       // [32 * nh] omega (mode 1)
   float* gl;       // [32 * nh] lambda gradient (new -> old)
-  float* md;       // [32 * nh] gradient of M^new
-  float* diff;     // [32 * nh] m1 - m0 (recorded)
-  float* tmp;      // [32 * nh] variable ids, then gathered S-dot, then S-dot contributions
+  int* var;        // [32 * nh] variable of the slot (-1: padding)
   int nmax, nh;
 };
 
@@ -47,7 +46,6 @@ struct AdjSmem {
 #define A2(n) s.a2[(n) * kWarp + lane]
 #define META(n) s.meta[(n) * kWarp + lane]
 
-template <int MODE>
 __device__ __forceinline__ AdjSmem carve_adj(unsigned char* p, const Tile& T) {
   AdjSmem s;
   s.nmax = T.nmax;
@@ -57,32 +55,40 @@ __device__ __forceinline__ AdjSmem carve_adj(unsigned char* p, const Tile& T) {
   p += (size_t)nn * 4;
   s.a2 = (float*)p;
   p += (size_t)nn * 4;
-  s.S = (float*)p;
-  p += (size_t)ns * 4;
-  s.al = (float*)p;
-  p += (size_t)ns * 4;
   s.gl = (float*)p;
   p += (size_t)ns * 4;
-  s.md = (float*)p;
+  s.var = (int*)p;
   p += (size_t)ns * 4;
-  s.diff = (float*)p;
-  p += (size_t)ns * 4;
-  s.tmp = (float*)p;
-  p += (size_t)ns * 4;
-  if (MODE == 1) {
-    s.om = (float*)p;
-    p += (size_t)ns * 4;
-  } else {
-    s.om = nullptr;
-  }
   s.meta = (uint16_t*)p;
   p += (size_t)nn * 2;
   s.desc = (uint16_t*)p;
   p += (size_t)ns * 2;
-  s.amin = (uint16_t*)p;
-  p += (size_t)ns * 2;
   s.code = (uint16_t*)p - 2 * kWarp;  // biased: element 32 n + lane is node number n
   return s;
+}
+
+// The per-slot inputs of one level's reverse step, for lane `lane`.
+struct LevelIn {
+  float S, al, om, md, diff, ga, go;
+  uint32_t amin;
+};
+
+template <int MODE>
+__device__ __forceinline__ LevelIn load_level(const DevArena& A, const AdjArgs& a, const AdjSmem& s, int64_t sb,
+                                              int h, int lane) {
+  LevelIn r;
+  const int q = h * kWarp + lane;
+  const int v = s.var[q];
+  r.diff = a.rec_diff[sb + q];
+  r.amin = a.rec_amin[sb + q];
+  r.S = v >= 0 ? a.S_in[v] : 0.0f;
+  r.al = MODE == 1 ? a.alpha[sb + q] : (v >= 0 ? __ldg(A.invdeg + v) : 0.0f);
+  r.om = MODE == 1 ? a.omega[sb + q] : a.omega0;
+  const float seed = a.seed_M ? a.seed_M[sb + q] : 0.0f;
+  r.md = seed + ((a.sdot_next && v >= 0) ? a.sdot_next[v] : 0.0f);  // gradient of M^new
+  r.ga = a.g_alpha[sb + q];
+  r.go = a.g_omega[sb + q];
+  return r;
 }
 
 }  // namespace
@@ -94,23 +100,16 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   const int tile = tile0 + blockIdx.x * (blockDim.x >> 5) + warp;
   if (tile >= tile1) return;
   const Tile T = A.tiles[tile];
-  AdjSmem s = carve_adj<MODE>(smem + (size_t)warp * region_bytes, T);
+  AdjSmem s = carve_adj(smem + (size_t)warp * region_bytes, T);
   const int ns = s.nh * kWarp;
   const int64_t sb = T.slot_base;
 
-  // ---- staging: the sweep's records, the gradients, the S^in gathers ----
+  // ---- staging: child codes, the sweep's node records, the gradients -----
   copy_async(s.code + 2 * kWarp, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
   copy_async(s.meta + 2 * kWarp, a.rec_meta + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
   copy_async(s.desc, A.desc + sb, ns * 2, lane);
-  copy_async(s.amin, a.rec_amin + sb, ns * 2, lane);
-  copy_async(s.diff, a.rec_diff + sb, ns * 4, lane);
   copy_async(s.gl, a.g_lam + sb, ns * 4, lane);
-  copy_async(s.tmp, A.slot_var + sb, ns * 4, lane);
-  if (MODE == 1) {
-    copy_async(s.om, a.omega + sb, ns * 4, lane);
-    copy_async(s.al, a.alpha + sb, ns * 4, lane);
-  }
-  if (a.seed_M) copy_async(s.md, a.seed_M + sb, ns * 4, lane);
+  copy_async(s.var, A.slot_var + sb, ns * 4, lane);
   cp_async_commit();
   // gradient accumulators of SP(., T) and SP(r, .)
   for (int n = 0; n < s.nmax; ++n) {
@@ -119,46 +118,19 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   }
   cp_async_wait_all();
   __syncwarp();
-  {
-    int* sv = reinterpret_cast<int*>(s.tmp);
-    const uint64_t pol = l2_evict_last();
-    for (int q = lane; q < ns; q += kWarp) {
-      const int v = sv[q];
-      if (!a.seed_M) s.md[q] = 0.0f;
-      if (v >= 0) {
-        cp_async4(s.S + q, a.S_in + v, pol);
-        if (MODE == 0) cp_async4(s.al + q, A.invdeg + v, pol);
-        if (a.sdot_next)
-          cp_async4(s.tmp + q, a.sdot_next + v, pol);
-        else
-          s.tmp[q] = 0.0f;
-      } else {
-        s.S[q] = 0.0f;
-        if (MODE == 0) s.al[q] = 0.0f;
-        s.tmp[q] = 0.0f;
-      }
-    }
-    cp_async_commit();
-  }
-  wait_gathers();
-  for (int q = lane; q < ns; q += kWarp) s.md[q] += s.tmp[q];  // gradient of M^new
-  __syncwarp();
 
   // ---- reverse ------------------------------------------------------------
   // one step of the reverse: the update and the min-marginal argmins of level h
-  auto reverse_level = [&](int h) {
+  auto reverse_level = [&](int h, const LevelIn& in) {
     const int q = h * kWarp + lane;
     const float g = s.gl[q];
-    const float al = s.al[q];
-    const float om = MODE == 1 ? s.om[q] : a.omega0;
-    const float Mt = s.md[q] - g;
-    s.tmp[q] = al * g;                                       // contribution to S-dot
-    a.g_alpha[sb + q] += g * s.S[q];
-    a.g_omega[sb + q] += Mt * s.diff[q];
-    const float dm1 = om * Mt, dm0 = -om * Mt;
+    const float Mt = in.md - g;
+    a.sdot[sb + q] = in.al * g;                              // contribution to S-dot
+    a.g_alpha[sb + q] = in.ga + g * in.S;
+    a.g_omega[sb + q] = in.go + Mt * in.diff;
+    const float dm1 = in.om * Mt, dm0 = -in.om * Mt;
     s.gl[q] = g + dm1;                                       // gradient of lambda^old
-    const uint32_t am = s.amin[q];
-    const int v0 = am & 0xFFu, v1 = am >> 8;
+    const int v0 = in.amin & 0xFFu, v1 = in.amin >> 8;
     const uint32_t c0 = node_code(s.code, v0, lane), c1 = node_code(s.code, v1, lane);
     A2(v0) += dm0;
     A1(c0 & 0xFFu) += dm0;  // terminals absorb into their unused entries
@@ -166,23 +138,28 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
     A1(c1 >> 8) += dm1;
   };
   if (FWD) {
+    LevelIn cur = load_level<MODE>(A, a, s, sb, s.nh - 1, lane);
     for (int h = s.nh - 1; h >= 0; --h) {
+      // the next level's inputs are loaded while this level is worked on
+      const LevelIn nxt = load_level<MODE>(A, a, s, sb, h > 0 ? h - 1 : 0, lane);
       const uint32_t ds = s.desc[h * kWarp + lane];
-      if (desc_width(ds) == 0) continue;
-      const int q = h * kWarp + lane;
-      const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
-      const int wn = desc_width(dn), fnn = desc_first(dn);
-      // SP(r, .) of level h+1 was relaxed from level h with lambda^new_h
-      float g = s.gl[q];
-      for (int r = 0; r < wn; ++r) {
-        const int wnode = fnn + r;
-        const float gd = A2(wnode);
-        const uint32_t mt = META(wnode);
-        A2(mt & 0xFFu) += gd;
-        if (mt & (1u << 8)) g += gd;
+      if (desc_width(ds) > 0) {
+        const int q = h * kWarp + lane;
+        const uint32_t dn = h + 1 < s.nh ? s.desc[(h + 1) * kWarp + lane] : 0u;
+        const int wn = desc_width(dn), fnn = desc_first(dn);
+        // SP(r, .) of level h+1 was relaxed from level h with lambda^new_h
+        float g = s.gl[q];
+        for (int r = 0; r < wn; ++r) {
+          const int wnode = fnn + r;
+          const float gd = A2(wnode);
+          const uint32_t mt = META(wnode);
+          A2(mt & 0xFFu) += gd;
+          if (mt & (1u << 8)) g += gd;
+        }
+        s.gl[q] = g;
+        reverse_level(h, cur);
       }
-      s.gl[q] = g;
-      reverse_level(h);
+      cur = nxt;
     }
     // SP(., T) under lambda^old: route its gradient top-down along argmin out-arcs
     for (int h = 0; h < s.nh; ++h) {
@@ -206,10 +183,12 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
       s.gl[q] = g;
     }
   } else {
+    LevelIn cur = load_level<MODE>(A, a, s, sb, 0, lane);
     for (int h = 0; h < s.nh; ++h) {
       const uint32_t ds = s.desc[h * kWarp + lane];
       const int w = desc_width(ds);
       if (w == 0) break;
+      const LevelIn nxt = load_level<MODE>(A, a, s, sb, h + 1 < s.nh ? h + 1 : h, lane);
       const int fn = desc_first(ds);
       const int q = h * kWarp + lane;
       // SP(., T) of level h was recomputed with lambda^new_h
@@ -226,7 +205,8 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
         }
       }
       s.gl[q] = g;
-      reverse_level(h);
+      reverse_level(h, cur);
+      cur = nxt;
     }
     // SP(r, .) under lambda^old: route its gradient bottom-up along argmin in-arcs
     for (int h = s.nh - 1; h >= 1; --h) {
@@ -251,7 +231,6 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   for (int q = lane; q < ns; q += kWarp) {
     if (desc_width(s.desc[q]) == 0) continue;
     a.g_lam[sb + q] = s.gl[q];
-    a.sdot[sb + q] = s.tmp[q];
   }
 }
 
