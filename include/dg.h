@@ -156,6 +156,17 @@ dg_status dg_get_stats(const dg_arena* arena, dg_stats* stats);
 dg_status dg_launch_group(const dg_plan_t* plan, int32_t g, int32_t* tile0, int32_t* tile1, int32_t* region_bytes,
                           int32_t* stream);
 
+/* Host-side check of the arena image a plan will upload: contiguous tiles,
+ * well-formed level descriptors, every child code inside the next level (or
+ * a terminal; only terminals below the last level), padding slots unused, a
+ * bijective slot map, variable lists and ELL columns that point back at
+ * their own slots, launch groups with enough shared memory for their tiles,
+ * bound chunks that cover every instance.  The kernels index memory with
+ * these numbers unchecked; a plan from dg_plan always passes.  DG_OK, or
+ * DG_EINVAL with the first violation in dg_last_error().  One pass over the
+ * image (no device work). */
+dg_status dg_plan_validate(const dg_plan_t* plan);
+
 /* slot_to_csr[q] = CSR position (row_ptr[j] + h) of arena slot q, or -1 for
  * padding (host array of num_slots entries). */
 dg_status dg_slot_map(const dg_plan_t* plan, int64_t* slot_to_csr);

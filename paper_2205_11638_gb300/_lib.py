@@ -81,6 +81,7 @@ SIGNATURES = {
                                           ctypes.POINTER(dg_options)]),
     "dg_backward_checkpointed": (c_int32, [P, P, P, P, c_int32, c_int32, c_int32, P, P, P, P, P, P, P, c_size_t,
                                            ctypes.POINTER(dg_options)]),
+    "dg_plan_validate": (c_int32, [P]),
     "dg_graph_create": (c_int32, [P, P, P, P, P, P, c_int32, c_int32, P, ctypes.POINTER(dg_options), PP]),
     "dg_graph_replay": (c_int32, [P, P]),
     "dg_graph_destroy": (None, [P]),

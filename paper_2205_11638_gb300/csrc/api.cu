@@ -176,6 +176,11 @@ dg_status dg_launch_group(const dg_plan_t* plan, int32_t g, int32_t* tile0, int3
   return DG_OK;
 }
 
+dg_status dg_plan_validate(const dg_plan_t* plan) {
+  if (!plan) return fail(DG_EINVAL, "dg_plan_validate: null plan");
+  return validate_plan(plan->p);
+}
+
 dg_status dg_slot_map(const dg_plan_t* plan, int64_t* out) {
   if (!plan || !out) return fail(DG_EINVAL, "dg_slot_map: null argument");
   std::memcpy(out, plan->p.slot_to_csr.data(), plan->p.slot_to_csr.size() * sizeof(int64_t));

@@ -508,4 +508,134 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   return DG_OK;
 }
 
+// Structural invariants of the arena image, checked on the host (the kernels
+// index shared and global memory with these numbers without bounds checks).
+dg_status validate_plan(const Plan& P) {
+  auto bad = [](const std::string& m) { return fail(DG_EINVAL, "dg_plan_validate: " + m); };
+  const int32_t n = P.sizes.n;
+  const int64_t m = P.sizes.m, NS = P.sizes.num_slots, NL = P.sizes.num_lambda;
+  const int64_t T = (int64_t)P.tiles.size();
+  if ((int64_t)P.desc.size() != NS || (int64_t)P.slot_var.size() != NS || (int64_t)P.slot_row.size() != NS ||
+      (int64_t)P.slot_to_csr.size() != NS || (int64_t)P.lohi8.size() != P.sizes.num_nodes_padded)
+    return bad("array sizes disagree with the plan sizes");
+  // tiles: contiguous bases, sane shapes, every lane's BDD well formed
+  int64_t node_base = 0, slot_base = 0, real_nodes = 0, real_slots = 0;
+  std::vector<int64_t> csr_seen(NL, 0);
+  for (int64_t t = 0; t < T; ++t) {
+    const Tile& tl = P.tiles[t];
+    const std::string at = "tile " + std::to_string(t) + ": ";
+    if (tl.node_base != node_base || tl.slot_base != slot_base) return bad(at + "bases not contiguous");
+    if (tl.nbdd < 1 || tl.nbdd > kWarp || tl.nhops < 1 || tl.nmax < 3 || tl.nmax > kMaxNodesPerBdd + 2 ||
+        tl.maxw < 1 || tl.maxw > kMaxWidth || tl.ring != ring_size(tl.maxw))
+      return bad(at + "shape out of range");
+    for (int b = 0; b < kWarp; ++b) {
+      int first = 2, level_w = 0, last_h = -1, row = -1;
+      for (int h = 0; h < tl.nhops; ++h) {
+        const int64_t q = slot_base + (int64_t)h * kWarp + b;
+        const int f = P.desc[q] & 0xFF, w = P.desc[q] >> 8;
+        if (b >= tl.nbdd || last_h >= 0) {
+          if (P.desc[q] != 0 || P.slot_var[q] != -1 || P.slot_to_csr[q] != -1)
+            return bad(at + "padding slot in use");
+          continue;
+        }
+        if (w == 0) {
+          if (h == 0) return bad(at + "lane without a BDD");
+          last_h = h - 1;
+          if (P.slot_var[q] != -1 || P.slot_to_csr[q] != -1) return bad(at + "padding slot in use");
+          continue;
+        }
+        if (f != first || (h == 0 && w != 1) || w > tl.maxw || f + w > tl.nmax)
+          return bad(at + "level descriptor inconsistent");
+        if (P.slot_var[q] < 0 || P.slot_var[q] >= n) return bad(at + "variable id out of range");
+        if (row < 0) row = P.slot_row[q];
+        if (P.slot_row[q] != row || row < 0 || row >= m) return bad(at + "slot rows of a lane differ");
+        const int64_t c = P.slot_to_csr[q];
+        if (c < 0 || c >= NL || csr_seen[c]++) return bad(at + "slot map not a bijection");
+        first = f + w;
+        level_w = w;
+        real_slots++;
+        real_nodes += w;
+      }
+      if (b >= tl.nbdd) continue;
+      if (last_h < 0) last_h = tl.nhops - 1;
+      // children: next level's nodes (no level skipped) or the bottom; the
+      // last level only the terminals; at least one child not the bottom
+      int f = 2;
+      for (int h = 0; h <= last_h; ++h) {
+        const int64_t q = slot_base + (int64_t)h * kWarp + b;
+        const int w = P.desc[q] >> 8;
+        const int fn = f + w;
+        const int wn = h < last_h ? (P.desc[q + kWarp] >> 8) : 0;
+        for (int r = 0; r < w; ++r) {
+          const uint32_t code = P.lohi8[node_base + (int64_t)(f + r - 2) * kWarp + b];
+          const uint32_t ch[2] = {code & 0xFFu, code >> 8};
+          if (ch[0] == (uint32_t)kBotCode && ch[1] == (uint32_t)kBotCode) return bad(at + "node with no path to top");
+          for (uint32_t c : ch) {
+            const bool term = c == (uint32_t)kTopCode || c == (uint32_t)kBotCode;
+            if (h == last_h ? !term : (c == (uint32_t)kTopCode || (!term && (c < (uint32_t)fn || c >= (uint32_t)(fn + wn)))))
+              return bad(at + "child code outside the next level");
+          }
+        }
+        f = fn;
+      }
+      (void)level_w;
+    }
+    node_base += (int64_t)(tl.nmax - 2) * kWarp;
+    slot_base += (int64_t)tl.nhops * kWarp;
+  }
+  if (node_base != P.sizes.num_nodes_padded || slot_base != NS) return bad("tiles do not cover the arrays");
+  if (real_slots != NL || real_nodes != P.sizes.num_nodes) return bad("slot or node count mismatch");
+  // variables: CSR and ELL columns point back at their own slots, rows ascending
+  if ((int64_t)P.var_ptr.size() != (int64_t)n + 1 || P.var_ptr[0] != 0 || P.var_ptr[n] != NL)
+    return bad("variable pointers malformed");
+  for (int32_t i = 0; i < n; ++i) {
+    if (P.var_ptr[i + 1] < P.var_ptr[i]) return bad("variable pointers not monotone");
+    int prev_row = -1;
+    for (int32_t k = P.var_ptr[i]; k < P.var_ptr[i + 1]; ++k) {
+      const int32_t q = P.var_slots[k];
+      if (q < 0 || q >= NS || P.slot_var[q] != i) return bad("variable " + std::to_string(i) + ": slot list wrong");
+      if (P.slot_row[q] <= prev_row) return bad("variable " + std::to_string(i) + ": rows not ascending");
+      prev_row = P.slot_row[q];
+    }
+    const int d = P.var_ptr[i + 1] - P.var_ptr[i];
+    for (int r = 0; r < kEll; ++r) {
+      int32_t e = P.var_ell[(size_t)r * n + i];
+      if (d > kEll && r == kEll - 1) {
+        if (e > -2) return bad("variable " + std::to_string(i) + ": ELL overflow mark missing");
+        e = -2 - e;
+      }
+      const int32_t want = r < d ? P.var_slots[P.var_ptr[i] + r] : -1;
+      if (e != want) return bad("variable " + std::to_string(i) + ": ELL column disagrees with the slot list");
+    }
+  }
+  // launch groups cover the tiles in order
+  int32_t t0 = 0;
+  for (const LaunchGroup& g : P.groups) {
+    if (g.tile0 != t0 || g.tile1 <= g.tile0 || g.stream < 0 || g.stream >= kStreams) return bad("launch groups malformed");
+    for (int32_t t = g.tile0; t < g.tile1; ++t) {
+      const Tile& tl = P.tiles[t];
+      if ((size_t)g.region_bytes < sweep_smem_bytes(tl.nmax, tl.nhops, 1, tl.ring) ||
+          (size_t)g.region_bwd1 < sweep_smem_bytes_bwd(tl.nmax, tl.nhops, 1) ||
+          g.meta_bytes < (tl.nmax - 2) * kWarp * 2)
+        return bad("launch group " + std::to_string(t0) + ": shared memory smaller than a tile needs");
+    }
+    t0 = g.tile1;
+  }
+  if (t0 != T) return bad("launch groups do not cover the tiles");
+  // bound chunks: per instance its rows, then its variables, in order
+  const int ni = P.sizes.num_inst;
+  for (int k = 0; k < ni; ++k) {
+    int64_t rows_at = P.inst_row_ptr[k], vars_at = P.inst_var_ptr[k];
+    for (int32_t c = P.inst_chunk_ptr[k]; c < P.inst_chunk_ptr[k + 1]; ++c) {
+      const int32_t* ch = &P.lb_chunks[(size_t)c * 4];
+      if (ch[0] != k || ch[3] <= ch[2]) return bad("bound chunk malformed");
+      int64_t& at = ch[1] == 0 ? rows_at : vars_at;
+      if (ch[2] != at) return bad("bound chunks leave a gap");
+      at = ch[3];
+    }
+    if (rows_at != P.inst_row_ptr[k + 1] || vars_at != P.inst_var_ptr[k + 1]) return bad("bound chunks do not cover an instance");
+  }
+  return DG_OK;
+}
+
 }  // namespace dg

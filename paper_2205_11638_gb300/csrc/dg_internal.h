@@ -169,6 +169,7 @@ inline size_t adjoint_smem_bytes(int nmax, int nhops, int mode) {
 }
 
 dg_status build_plan(const dg_rows* rows, const dg_options* opts, Plan& plan);
+dg_status validate_plan(const Plan& plan);
 
 // error reporting
 dg_status fail(dg_status st, const std::string& msg);

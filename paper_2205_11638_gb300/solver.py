@@ -99,6 +99,10 @@ class Plan:
         check(lib.dg_bdd_export(self._h, int(j), _ptr(ls), _ptr(lo), _ptr(hi), ctypes.byref(nn)), "dg_bdd_export")
         return ls, lo, hi
 
+    def validate(self):
+        """dg_plan_validate: structural invariants of the arena image (raises on a violation)."""
+        check(_lib.load().dg_plan_validate(self._h), "dg_plan_validate")
+
     def launch_groups(self):
         """[(tile0, tile1, per-warp shared bytes, stream)] of the sweep launches."""
         out = []

@@ -51,12 +51,14 @@ def _check_iterations(prob, iters_lam=1, iters_lb=100, omega=None, alpha=None, *
     if omega is not None:
         om_t, al_t = A.from_csr(omega), A.from_csr(alpha)
     A.iterate(lam, M, om_t, al_t, iters=iters_lam)
+    assert torch.isfinite(lam).all() and torch.isfinite(M).all()
     ol1, oM1 = O.iterate(ol, oM, 0.5 if omega is None else omega, alpha, iters_lam)
     err_l = np.abs(_np(A.to_csr(lam)) - ol1).max()
     err_M = np.abs(_np(A.to_csr(M)) - oM1).max()
     assert err_l <= TOL_LAM * cmax, err_l
     assert err_M <= TOL_LAM * cmax, err_M
     lb = A.iterate(lam, M, om_t, al_t, iters=iters_lb - iters_lam, lb=True)
+    assert torch.isfinite(lam).all() and torch.isfinite(M).all() and torch.isfinite(lb).all()
     olT, oMT = O.iterate(ol1, oM1, 0.5 if omega is None else omega, alpha, iters_lb - iters_lam)
     want = O.lower_bound(olT, oMT, per_instance=True)[1]
     got = lb.cpu().numpy()
@@ -271,3 +273,21 @@ def test_batched_uncovered_variables_per_instance():
     ol, oM = O.iterate(ol, oM, 0.5, None, 30)
     want = O.lower_bound(ol, oM, per_instance=True)[1]
     np.testing.assert_allclose(got, want, rtol=TOL_LB, atol=TOL_LB)
+
+
+def test_resume_from_saved_state_is_bit_identical():
+    """Solver resume: the arena is rebuilt from the rows and the saved (lambda,
+    M) continue exactly where they stopped: 6 + 4 iterations through a second,
+    independently planned arena equal 10 iterations in one call."""
+    prob = workloads.independent_set(n=3000, seed=21)
+    A = _arena(prob)
+    lam, M = A.init_lambda()
+    lb10 = A.iterate(lam, M, iters=10, lb=True)
+    B = _arena(prob)
+    l2, m2 = B.init_lambda()
+    B.iterate(l2, m2, iters=6)
+    saved = (l2.cpu(), m2.cpu())
+    C = _arena(prob)
+    l3, m3 = saved[0].to(C.device), saved[1].to(C.device)
+    lb6_4 = C.iterate(l3, m3, iters=4, lb=True)
+    assert torch.equal(l3, lam) and torch.equal(m3, M) and torch.equal(lb6_4, lb10)

@@ -153,3 +153,48 @@ def test_calls_on_missing_arena_fail_cleanly():
                                         None, 0, None) == _lib.DG_ESTATE
     assert lib.dg_graph_replay(None, None) == _lib.DG_EINVAL
     assert b"null" in lib.dg_last_error()
+
+
+@pytest.mark.parametrize("make", [lambda: workloads.set_cover(), lambda: workloads.independent_set(n=1500, seed=4),
+                                  lambda: workloads.matching_quadratic(L=30, R=30, pairs=900, seed=5),
+                                  lambda: workloads.tracking(frames=6, dets=200, seed=6),
+                                  lambda: workloads.batched_mix(num=6, scale=0.03)[0]])
+def test_plans_pass_the_validator(make):
+    """Every plan the builder makes satisfies the arena invariants the kernels
+    rely on (dg_plan_validate), also under non-default layout options."""
+    rows = make()
+    solver.plan(rows).validate()
+    solver.plan(rows, chunk_rows=64, group_ratio_pct=50).validate()
+
+
+def test_validator_catches_each_corruption(tmp_path):
+    """The validator is not vacuous: a host harness builds a plan with the
+    library's builder, breaks one invariant at a time and every broken copy
+    is rejected while the intact one passes."""
+    from paper_2205_11638_gb300 import build as B
+    csrc = os.path.join(ROOT, "paper_2205_11638_gb300", "csrc")
+    exe = tmp_path / "validate_harness"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-pthread", f"-I{os.path.join(B.CUDA_HOME, 'include')}",
+                           f"-I{os.path.join(ROOT, 'include')}", f"-I{csrc}",
+                           os.path.join(ROOT, "tests", "validate_harness.cpp"), os.path.join(csrc, "builder.cpp"),
+                           "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).strip().splitlines()
+    res = {ln.split("|")[0]: (int(ln.split("|")[1]), ln.split("|", 2)[2]) for ln in out}
+    assert res.pop("intact") == (0, "")
+    assert len(res) == 10
+    for name, (st, msg) in res.items():
+        assert st == _lib.DG_EINVAL and msg.startswith("dg_plan_validate:"), (name, st, msg)
+
+
+def test_plan_is_deterministic():
+    """The arena is rebuilt from the rows alone (solver resume saves only
+    lambda and M): two plans of the same rows, built with several host
+    threads, have the same layout."""
+    rows = workloads.tracking(frames=6, dets=200, seed=9)
+    P1 = solver.plan(rows, num_threads=4)
+    P2 = solver.plan(rows, num_threads=3)
+    assert np.array_equal(P1.slot_to_csr, P2.slot_to_csr)
+    assert P1.launch_groups() == P2.launch_groups()
+    for j in (0, 7, len(rows["row_ptr"]) - 2):
+        for a, b in zip(P1.bdd(j), P2.bdd(j)):
+            assert np.array_equal(a, b)
