@@ -258,7 +258,10 @@ size_t dg_backward_workspace_bytes(const dg_arena* arena, int32_t iters, int32_t
  * (arena order; g_omega / g_alpha accumulate over all blocks as in Alg. 2,
  * for mode 0 they are the gradients of the per-slot values the scalar
  * expands to).  The forward pass is recomputed from checkpoints of (lam, M)
- * kept every ckpt_every iterations in workspace. */
+ * kept every ckpt_every iterations in workspace; each segment between two
+ * checkpoints is re-run as recording sweeps whose argmins (per node and per
+ * slot) the adjoint sweeps then read back.  opts->renorm_every must be 0 (the
+ * FP64 re-projection is not differentiated): DG_EINVAL otherwise. */
 dg_status dg_backward(dg_arena* arena, void* stream, const float* lam0, const float* M0, const float* omega,
                       const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
                       const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,

@@ -699,6 +699,9 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_backward: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_backward: mode 1 needs omega and alpha");
   if (iters < 0) return fail(DG_EINVAL, "dg_backward: negative iteration count");
+  if (opts && opts->renorm_every > 0)
+    return fail(DG_EINVAL, "dg_backward: the adjoint does not differentiate the FP64 re-projection "
+                           "(renorm_every must be 0)");
   if (dg_status s = check_vectors("dg_backward", lam0, M0, omega, alpha)) return s;
   if (dg_status s = check_vectors("dg_backward", g_lam_T, g_M_T, g_lam0, g_M0)) return s;
   if (dg_status s = check_vectors("dg_backward", g_omega, g_alpha)) return s;

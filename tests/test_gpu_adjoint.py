@@ -182,11 +182,15 @@ def test_checkpointed_forward_and_backward_are_bit_identical(per_slot):
 
 
 def test_checkpointed_forward_rejects_renorm():
+    """The FP64 re-projection is not differentiated: both the checkpointing
+    forward and dg_backward refuse options that ask for it."""
     prob = workloads.matching_quadratic(L=20, R=20, pairs=200, seed=2)
     A = solver.plan(prob, renorm_every=5).bind()
     lam, M = A.init_lambda()
     with pytest.raises(RuntimeError, match="re-projection"):
         A.iterate_checkpointed(lam, M, iters=3, ckpt_every=2)
+    with pytest.raises(RuntimeError, match="re-projection"):
+        A.backward(lam, M, None, None, 3, 2, A.zeros(), A.zeros())
 
 
 @pytest.mark.parametrize("T,ck", [(0, 3), (2, 50), (5, 1)])
