@@ -706,7 +706,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   if (dg_status s = check_vectors("dg_backward", g_lam_T, g_M_T, g_lam0, g_M0)) return s;
   if (dg_status s = check_vectors("dg_backward", g_omega, g_alpha)) return s;
   for (const AdjGroup& g : ar->adj_groups)
-    if ((size_t)(mode ? g.region1 : g.region0) > ar->cta_smem_cap)
+    if ((size_t)g.region > ar->cta_smem_cap)
       return fail(DG_EINVAL, "dg_backward: a tile's adjoint state does not fit one CTA's shared memory");
   for (const LaunchGroup& g : ar->groups)
     if ((size_t)(mode ? g.region_bwd1 : g.region_bwd0) + (size_t)g.meta_bytes > ar->cta_smem_cap ||

@@ -357,7 +357,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     tile.maxw = maxw;
     tile.ring = ring_size(maxw);
     smem_max = std::max(smem_max, sweep_smem_bytes(nmax, nh, 1, tile.ring));
-    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nmax, nh, 1));
+    smem_adj_max = std::max(smem_adj_max, adjoint_smem_bytes(nmax, nh));
     P.max_tile_rows = std::max(P.max_tile_rows, nmax);
     P.max_tile_slots = std::max<int32_t>(P.max_tile_slots, (int32_t)tslots);
     P.max_tile_hops = std::max(P.max_tile_hops, nh);
@@ -407,11 +407,9 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     }
   }
   for (const LaunchGroup& g : P.groups) {
-    AdjGroup a{g.tile0, g.tile1, 0, 0, g.stream, 0};
-    for (int t = g.tile0; t < g.tile1; ++t) {
-      a.region0 = std::max<int32_t>(a.region0, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 0));
-      a.region1 = std::max<int32_t>(a.region1, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops, 1));
-    }
+    AdjGroup a{g.tile0, g.tile1, 0, g.stream};
+    for (int t = g.tile0; t < g.tile1; ++t)
+      a.region = std::max<int32_t>(a.region, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops));
     P.adj_groups.push_back(a);
   }
   const int64_t num_slots = slot_base;

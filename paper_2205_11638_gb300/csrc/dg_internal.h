@@ -102,9 +102,8 @@ struct LaunchGroup {
 // shared-memory footprint).
 struct AdjGroup {
   int32_t tile0, tile1;
-  int32_t region0, region1;  // per-warp slice, mode 0 / mode 1
+  int32_t region;  // per-warp slice (the same in both modes)
   int32_t stream;
-  int32_t pad;
 };
 
 struct Plan {
@@ -161,10 +160,9 @@ inline size_t sweep_smem_bytes_bwd(int nmax, int nhops, int mode) {
 // the child codes per node; per slot the descriptor, the lambda gradient and
 // the variable (the other per-slot inputs of the reverse are read into
 // registers a level ahead, the same in both modes).
-inline size_t adjoint_smem_bytes(int nmax, int nhops, int mode) {
+inline size_t adjoint_smem_bytes(int nmax, int nhops) {
   const size_t nn = (size_t)nmax * kWarp, ns = (size_t)nhops * kWarp;
   size_t b = nn * 10 + ns * 10 + (size_t)(nmax - 2) * kWarp * 2;
-  (void)mode;
   return (b + 127) / 128 * 128;
 }
 

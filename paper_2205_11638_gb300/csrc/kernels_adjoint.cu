@@ -254,7 +254,7 @@ static void launch_adj(const DevArena& A, const AdjArgs& a, const AdjGroup* grou
   if (fork) ss.begin();
   for (int g = 0; g < num_groups; ++g) {
     const AdjGroup& G = groups[g];
-    const size_t region = (size_t)(MODE == 1 ? G.region1 : G.region0);
+    const size_t region = (size_t)G.region;
     const int wpc = best_warps_per_cta(region, 4, cap);
     const int nt = G.tile1 - G.tile0;
     k_adjoint<FWD, MODE><<<(nt + wpc - 1) / wpc, wpc * kWarp, region * wpc, fork ? ss.of(G.stream) : ss.main>>>(
