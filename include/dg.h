@@ -22,7 +22,8 @@
  *    float32 arrays of dg_sizes.num_slots entries in the order of the arena
  *    (tiles of BDDs, hop-major inside a tile, padded).  dg_slot_map gives the
  *    CSR position of every arena slot; padding slots map to -1 and are kept
- *    at 0 by every call.
+ *    at 0 by every call.  A problem without rows has no slots: its state
+ *    vectors may then be NULL.
  *  - Status codes: DG_EINVAL for malformed input, DG_EINFEASIBLE when a row
  *    has no feasible assignment, DG_EFORCED when a row fixes one of its
  *    variables (min-marginal of one value infinite; presolve is the caller's

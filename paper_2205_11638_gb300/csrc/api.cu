@@ -103,6 +103,9 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   return check_launch("dg_iterate");
 }
 
+// A state vector may be NULL only when the arena has no slots (no rows).
+bool missing(const dg_arena* ar, const void* p) { return p == nullptr && ar->sizes.num_slots > 0; }
+
 dg_status check_state(const dg_arena* ar) {
   if (!ar) return fail(DG_ESTATE, "null arena");
   return DG_OK;
@@ -350,7 +353,7 @@ dg_status dg_get_stats(const dg_arena* arena, dg_stats* stats) {
 
 dg_status dg_init_lambda(dg_arena* ar, void* stream, float* lam, float* M) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M) return fail(DG_EINVAL, "dg_init_lambda: null state");
+  if (missing(ar, lam) || missing(ar, M)) return fail(DG_EINVAL, "dg_init_lambda: null state");
   launch_init(ar->dev, lam, M, (cudaStream_t)stream);
   return check_launch("dg_init_lambda");
 }
@@ -358,7 +361,7 @@ dg_status dg_init_lambda(dg_arena* ar, void* stream, float* lam, float* M) {
 dg_status dg_iterate(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
                      int32_t mode, int32_t iters, double* lb_out, const dg_options* opts) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M) return fail(DG_EINVAL, "dg_iterate: null state");
+  if (missing(ar, lam) || missing(ar, M)) return fail(DG_EINVAL, "dg_iterate: null state");
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_iterate: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_iterate: mode 1 needs omega and alpha");
   if (iters < 0) return fail(DG_EINVAL, "dg_iterate: negative iteration count");
@@ -469,7 +472,7 @@ dg_status dg_sum_M(dg_arena* ar, void* stream, const float* M, float* lam, const
 dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
                    int32_t mode, int32_t forward, int32_t want_energy, const dg_options* opts) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M) return fail(DG_EINVAL, "dg_sweep: null state");
+  if (missing(ar, lam) || missing(ar, M)) return fail(DG_EINVAL, "dg_sweep: null state");
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_sweep: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_sweep: mode 1 needs omega and alpha");
   if (forward && want_energy) return fail(DG_EINVAL, "dg_sweep: energies come from backward sweeps");
@@ -496,7 +499,7 @@ dg_status dg_bound_from_energies(dg_arena* ar, void* stream, double* lb_out) {
 
 dg_status dg_min_marginals(dg_arena* ar, void* stream, const float* lam, float* m0, float* m1) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !m0 || !m1) return fail(DG_EINVAL, "dg_min_marginals: null pointer");
+  if (missing(ar, lam) || missing(ar, m0) || missing(ar, m1)) return fail(DG_EINVAL, "dg_min_marginals: null pointer");
   if (dg_status s = check_vectors("dg_min_marginals", lam, m0, m1)) return s;
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
@@ -509,7 +512,7 @@ dg_status dg_min_marginals(dg_arena* ar, void* stream, const float* lam, float* 
 
 dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const float* M, double* lb, float* E_per_row) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M || !lb) return fail(DG_EINVAL, "dg_lower_bound: null pointer");
+  if (missing(ar, lam) || missing(ar, M) || !lb) return fail(DG_EINVAL, "dg_lower_bound: null pointer");
   if (dg_status s = check_vectors("dg_lower_bound", lam, M)) return s;
   cudaStream_t st = (cudaStream_t)stream;
   SweepArgs a{};
@@ -528,7 +531,7 @@ dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const flo
 
 dg_status dg_lower_bound_noalloc(dg_arena* ar, void* stream, const float* lam, const float* M, double* lb) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M || !lb) return fail(DG_EINVAL, "dg_lower_bound_noalloc: null pointer");
+  if (missing(ar, lam) || missing(ar, M) || !lb) return fail(DG_EINVAL, "dg_lower_bound_noalloc: null pointer");
   if (dg_status s = check_vectors("dg_lower_bound_noalloc", lam, M)) return s;
   return lower_bound_noalloc(ar->dev, ar->groups.data(), (int)ar->groups.size(), threads_of(nullptr),
                              streams_for(ar, (cudaStream_t)stream), lam, M, lb);
@@ -536,7 +539,8 @@ dg_status dg_lower_bound_noalloc(dg_arena* ar, void* stream, const float* lam, c
 
 dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* M, float* g_lam, float* g_M) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M || !g_lam || !g_M) return fail(DG_EINVAL, "dg_lb_seed: null pointer");
+  if (missing(ar, lam) || missing(ar, M) || missing(ar, g_lam) || missing(ar, g_M))
+    return fail(DG_EINVAL, "dg_lb_seed: null pointer");
   if (dg_status s = check_vectors("dg_lb_seed", lam, g_lam)) return s;
   cudaStream_t st = (cudaStream_t)stream;
   SweepArgs a{};
@@ -841,7 +845,7 @@ dg_status dg_iterate_checkpointed(dg_arena* ar, void* stream, float* lam, float*
                                   const float* alpha, int32_t mode, int32_t iters, int32_t ckpt_every,
                                   void* workspace, size_t ws_bytes, double* lb_out, const dg_options* opts) {
   if (dg_status s = check_state(ar)) return s;
-  if (!lam || !M) return fail(DG_EINVAL, "dg_iterate_checkpointed: null state");
+  if (missing(ar, lam) || missing(ar, M)) return fail(DG_EINVAL, "dg_iterate_checkpointed: null state");
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_iterate_checkpointed: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_iterate_checkpointed: mode 1 needs omega and alpha");
   if (iters < 0) return fail(DG_EINVAL, "dg_iterate_checkpointed: negative iteration count");

@@ -291,3 +291,36 @@ def test_resume_from_saved_state_is_bit_identical():
     l3, m3 = saved[0].to(C.device), saved[1].to(C.device)
     lb6_4 = C.iterate(l3, m3, iters=4, lb=True)
     assert torch.equal(l3, lam) and torch.equal(m3, M) and torch.equal(lb6_4, lb10)
+
+
+def test_largest_bdd_and_widest_level_vs_oracle():
+    """The largest BDD the layout takes (254 nodes, 30 levels of width up to
+    15) next to a level of 17..32 nodes and ordinary rows, in one tile set:
+    lambda after one iteration and the bound after 60 against the oracle."""
+    rng = np.random.default_rng(33)
+    a, b = _wide_row(rng)
+    k = len(a)
+    n = 40
+    rows = [(np.arange(30), np.ones(30, np.int64), 0, 14),     # 254 nodes
+            (np.arange(k) + 20, a, 0, b)]                        # wide level
+    for r in workloads.random_rows(60, kmax=6, n=n, seed=34):
+        try:
+            oracle.Oracle(workloads.single_rows_problem([r], n, np.zeros(n)))
+            rows.append(r)
+        except oracle.OracleError:
+            pass
+    prob = workloads.single_rows_problem(rows, n, rng.normal(size=n))
+    assert len(solver.plan(prob).bdd(0)[1]) == 254
+    _check_iterations(prob, 1, 60)
+
+
+def test_problem_without_rows():
+    """Zero rows: iterating is a no-op and the bound is sum_i min(0, c_i)."""
+    c = np.array([1.0, -2, 3, -0.5, 0])
+    prob = dict(n=5, row_ptr=np.zeros(1, np.int64), col=np.zeros(0, np.int32), coef=np.zeros(0, np.int32),
+                sense=np.zeros(0, np.int8), rhs=np.zeros(0, np.int32), c=c)
+    A = _arena(prob)
+    lam, M = A.init_lambda()
+    lb = A.iterate(lam, M, iters=3, lb=True)
+    assert float(lb[0]) == float(np.minimum(c, 0).sum())
+    assert float(A.lower_bound(lam, M)[0]) == float(np.minimum(c, 0).sum())

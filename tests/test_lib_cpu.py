@@ -122,6 +122,30 @@ def test_status_codes():
     assert e.value.status == _lib.DG_EINVAL
 
 
+def test_bdd_node_limit():
+    """A BDD of exactly 254 nodes (x_0 + ... + x_29 <= 14) is accepted; one
+    more variable and a larger bound exceed the 8-bit node numbers and the
+    row is rejected with DG_EINVAL and a message naming it."""
+    ok = workloads.single_rows_problem([(np.arange(30), np.ones(30, np.int64), 0, 14)], 30, np.zeros(30))
+    P = solver.plan(ok)
+    assert len(P.bdd(0)[1]) == 254
+    P.validate()
+    big = workloads.single_rows_problem([(np.arange(60), np.ones(60, np.int64), 0, 30)], 60, np.zeros(60))
+    with pytest.raises(_lib.DgError, match="more than 254 nodes") as e:
+        solver.plan(big)
+    assert e.value.status == _lib.DG_EINVAL
+
+
+def test_problem_without_rows_plans_empty_arena():
+    """Zero rows: no tiles, no slots, no launch groups; every variable is
+    uncovered (its bound term is min(0, c_i))."""
+    prob = dict(n=5, row_ptr=np.zeros(1, np.int64), col=np.zeros(0, np.int32), coef=np.zeros(0, np.int32),
+                sense=np.zeros(0, np.int8), rhs=np.zeros(0, np.int32), c=np.array([1.0, -2, 3, -0.5, 0]))
+    P = solver.plan(prob)
+    assert (P.sizes.num_tiles, P.sizes.num_slots, P.sizes.num_launch_groups) == (0, 0, 0)
+    P.validate()
+
+
 def test_tile_budgets_respected():
     prob = workloads.tracking(frames=6, dets=60, seed=2)
     for tn, ts in [(256, 128), (1024, 512), (4096, 2048)]:
