@@ -324,3 +324,28 @@ def test_problem_without_rows():
     lb = A.iterate(lam, M, iters=3, lb=True)
     assert float(lb[0]) == float(np.minimum(c, 0).sum())
     assert float(A.lower_bound(lam, M)[0]) == float(np.minimum(c, 0).sum())
+
+
+def test_degenerate_parameters():
+    """omega = 0 moves nothing (M stays 0, so alpha S = 0 and lambda is
+    unchanged bit for bit); with every variable in one row (alpha = 1) the
+    bound at the initial split already equals the optimum and stays there."""
+    prob = workloads.matching_quadratic(L=20, R=20, pairs=200, seed=41)
+    A = _arena(prob)
+    lam0, M0 = A.init_lambda()
+    lam, M = lam0.clone(), M0.clone()
+    omega = torch.zeros_like(lam)
+    alpha = A.from_csr(1.0 / np.bincount(prob["col"], minlength=prob["n"])[prob["col"]])
+    A.iterate(lam, M, omega, alpha, iters=5)
+    assert torch.equal(lam, lam0) and torch.equal(M, M0)
+    # disjoint rows: x_{2r} + x_{2r+1} <= 1 for r < 20, random costs
+    rng = np.random.default_rng(42)
+    rows = [(np.array([2 * r, 2 * r + 1]), np.array([1, 1]), 0, 1) for r in range(20)]
+    c = rng.normal(size=40)
+    dis = workloads.single_rows_problem(rows, 40, c)
+    B = _arena(dis)
+    l, m = B.init_lambda()
+    opt = sum(min(0.0, c[2 * r], c[2 * r + 1]) for r in range(20))
+    assert abs(float(B.lower_bound(l, m)[0]) - opt) < 1e-5
+    lb = B.iterate(l, m, iters=10, lb=True)
+    assert abs(float(lb[0]) - opt) < 1e-5
