@@ -103,7 +103,7 @@ RowResult build_row(const int32_t* a, int k, int sense, int64_t rhs, RowScratch&
     if (!sc.uniq.empty() && sc.uniq.front() == 0u) sc.uniq.erase(sc.uniq.begin());  // (bottom, bottom)
     if (sc.uniq.size() > (size_t)kMaxWidth) {
       res.status = DG_EINVAL;
-      res.msg = "a BDD level has more than 32 nodes (one level must fit one warp)";
+      res.msg = "a BDD level has more than 128 nodes (child ranks are 8-bit)";
       return res;
     }
     for (size_t q = b; q < e; ++q) {

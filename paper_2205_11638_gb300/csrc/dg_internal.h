@@ -20,7 +20,7 @@ constexpr uint32_t kTopCode = 0u;
 constexpr uint32_t kBotCode = 1u;
 constexpr int kMaxNodesPerBdd = 254;
 constexpr int kWarp = 32;
-constexpr int kMaxWidth = 32;  // nodes of one BDD level
+constexpr int kMaxWidth = 128;  // nodes of one BDD level (child ranks are 8-bit)
 constexpr int kStreams = 4;    // streams one sweep's launch groups run on
 // The first kEll slots of every variable are also stored column by column
 // (var_ell[r * n + i], ELLPACK layout) so that the S reduction reads them

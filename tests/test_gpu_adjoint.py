@@ -215,3 +215,40 @@ def test_checkpointed_edge_intervals(T, ck):
         assert torch.equal(x, y)
     if T == 0:
         assert torch.equal(got[0], gl) and torch.equal(got[1], gM)
+
+
+def test_gpu_adjoint_wide_levels_vs_oracle():
+    """Alg. 2 through BDDs with a level wider than a warp (a knapsack row with
+    more than 40 nodes on one level) and the 30-level cardinality row at the
+    node limit, next to ordinary rows; per-slot parameters, 2 iterations."""
+    rng = np.random.default_rng(61)
+    while True:
+        k = int(rng.integers(8, 14))
+        a = rng.integers(1, 40, size=k)
+        b = int(a.sum() // 2)
+        try:
+            Ow = oracle.Oracle(workloads.single_rows_problem([(np.arange(k), a, 0, b)], k, np.zeros(k)))
+        except oracle.OracleError:
+            continue
+        ls, lo, _ = Ow.bdd(0)
+        if np.diff(ls).max() > 40 and len(lo) <= 254:
+            break
+    n = 36
+    rows = [(np.arange(k) + 3, a, 0, b), (np.arange(30) + 6, np.ones(30, np.int64), 0, 14)]
+    for r in workloads.random_rows(40, kmax=5, n=n, seed=62):
+        try:
+            oracle.Oracle(workloads.single_rows_problem([r], n, np.zeros(n)))
+            rows.append(r)
+        except oracle.OracleError:
+            pass
+    prob = workloads.single_rows_problem(rows, n, rng.normal(size=n))
+    O = oracle.Oracle(prob)
+    A = solver.plan(prob).bind()
+    lam, M, omega, alpha = (np.float32(x).astype(np.float64) for x in _params(O, 63))
+    a_ = np.float32(rng.normal(size=O.num_slots)).astype(np.float64)
+    b_ = np.float32(rng.normal(size=O.num_slots)).astype(np.float64)
+    want = O.backward(lam, M, omega, alpha, 2, a_, b_)
+    t = [A.from_csr(x) for x in (lam, M, omega, alpha, a_, b_)]
+    got = A.backward(t[0], t[1], t[2], t[3], 2, 1, t[4], t[5])
+    for g, w in zip(got, want):
+        np.testing.assert_allclose(_np(A.to_csr(g)), w, atol=1e-4, rtol=0)

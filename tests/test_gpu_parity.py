@@ -188,17 +188,18 @@ def test_graph_replay_equals_iterate():
         float(lb_out[0]) - float(A.lower_bound(lam, M)[0])) < 1e-9
 
 
-def _wide_row(rng, lo_w=17, hi_w=32):
+def _wide_row(rng, lo_w=17, hi_w=32, amax=25, kmax=13):
     while True:
-        k = int(rng.integers(8, 13))
-        a = rng.integers(1, 25, size=k)
+        k = int(rng.integers(8, kmax))
+        a = rng.integers(1, amax, size=k)
         b = int(a.sum() // 2)
         try:
             O = oracle.Oracle(workloads.single_rows_problem([(np.arange(k), a, 0, b)], k, np.zeros(k)))
         except oracle.OracleError:
             continue
-        w = np.diff(O.bdd(0)[0]).max()
-        if lo_w <= w <= hi_w:
+        ls, lo, _ = O.bdd(0)
+        w = np.diff(ls).max()
+        if lo_w <= w <= hi_w and len(lo) <= 254:
             return a, b
 
 
@@ -295,14 +296,17 @@ def test_resume_from_saved_state_is_bit_identical():
 
 def test_largest_bdd_and_widest_level_vs_oracle():
     """The largest BDD the layout takes (254 nodes, 30 levels of width up to
-    15) next to a level of 17..32 nodes and ordinary rows, in one tile set:
+    15) next to levels of 17..32 and of more than 40 nodes and ordinary rows:
     lambda after one iteration and the bound after 60 against the oracle."""
     rng = np.random.default_rng(33)
     a, b = _wide_row(rng)
     k = len(a)
+    a2, b2 = _wide_row(rng, lo_w=40, hi_w=128, amax=40, kmax=14)
+    k2 = len(a2)
     n = 40
     rows = [(np.arange(30), np.ones(30, np.int64), 0, 14),     # 254 nodes
-            (np.arange(k) + 20, a, 0, b)]                        # wide level
+            (np.arange(k) + 20, a, 0, b),                        # level of 17..32 nodes
+            (np.arange(k2) + 5, a2, 0, b2)]                      # level of more than 40 nodes
     for r in workloads.random_rows(60, kmax=6, n=n, seed=34):
         try:
             oracle.Oracle(workloads.single_rows_problem([r], n, np.zeros(n)))

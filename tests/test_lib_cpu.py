@@ -107,7 +107,7 @@ def _status_of(rows, n):
 def test_status_codes():
     assert _status_of([(np.array([0, 1]), np.array([2, 2]), 2, 1)], 2) == _lib.DG_EINFEASIBLE
     assert _status_of([(np.array([0, 1]), np.array([1, 1]), 1, 2)], 2) == _lib.DG_EFORCED
-    # a knapsack row whose BDD has a level of 112 nodes (wider than one warp)
+    # a knapsack row whose BDD has more than 254 nodes (a level of 112)
     a = np.array([28, 31, 45, 57, 3, 9, 49, 56, 15, 19, 52, 25, 17, 49, 16, 25])
     assert _status_of([(np.arange(16), a, 0, 248)], 16) == _lib.DG_EINVAL
     bad = workloads.single_rows_problem([(np.array([0, 1]), np.array([1, 1]), 0, 1)], 2, np.zeros(2))
