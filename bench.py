@@ -99,6 +99,10 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # the timed region starts only once the sampler is producing lines
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -173,7 +177,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    frames = 50
+    # one oracle iteration per step on a slice of the tracking generator,
+    # sized so that the whole run stays within about a minute of CPU time
+    # (about 3 ms per frame and iteration; fewer frames for many steps)
+    frames = int(max(3, min(50, 12000 // max(1, args.steps + args.warmup))))
     prob = workloads.tracking(frames=frames, dets=2000)
     O = oracle.Oracle(prob)
     lam, M = O.init_lambda()
@@ -464,7 +471,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tracking_500x2000", choices=sorted(WORKLOADS))
