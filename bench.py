@@ -203,6 +203,47 @@ def run_reference(args):
     return 0
 
 
+def _matching_adjoint_measurement(solver, torch, iters=20, ck=10, reps=5):
+    """The matching instance with linearised quadratic terms (200 x 200, 10
+    candidates, 20,000 pairs) and per-slot parameters (omega = sigmoid of
+    random logits, alpha = softmax of random logits over each variable's
+    rows): forward + adjoint of the final lower bound through 20 unrolled
+    iterations, in ms (mean of `reps` after one warm-up)."""
+    import numpy as np
+    prob = workloads.matching_quadratic()
+    A = solver.plan(prob).bind()
+    col, n = prob["col"], prob["n"]
+    rng = np.random.default_rng(3)
+    z = np.exp(rng.normal(size=len(col)))
+    s = np.zeros(n)
+    np.add.at(s, col, z)
+    alpha = A.from_csr(z / s[col])
+    omega = A.from_csr(1.0 / (1.0 + np.exp(-rng.normal(size=len(col)))))
+    lam0, M0 = A.init_lambda()
+    ws = torch.empty(A.backward_workspace_bytes(iters, ck), dtype=torch.uint8, device=A.device)
+    outs = [A.zeros() for _ in range(4)]
+    gl, gM = A.zeros(), A.zeros()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms = b_ms = 0.0
+    for rep in range(reps + 1):
+        lam, M = lam0.clone(), M0.clone()
+        torch.cuda.synchronize()
+        ev[0].record()
+        A.iterate_checkpointed(lam, M, omega, alpha, iters=iters, ckpt_every=ck, workspace=ws)
+        A.lb_seed_into(lam, M, gl, gM)
+        ev[1].record()
+        A.backward_checkpointed(omega, alpha, iters, ck, gl, gM, ws, outs)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if rep > 0:
+            f_ms += ev[0].elapsed_time(ev[1]) / reps
+            b_ms += ev[1].elapsed_time(ev[2]) / reps
+    return {"workload": "matching_quadratic_200", "N_lambda": int(A.stats.sizes.num_lambda),
+            "unrolled_iterations": iters, "checkpoint_every": ck, "parameters": "per-slot omega, alpha",
+            "forward_ms": f_ms, "backward_ms": b_ms, "fwd_adjoint_ms": f_ms + b_ms,
+            "loss": "lower bound (eq. 3 plus unary term)"}
+
+
 def _batched_measurement(args, solver, torch, iters=50, ck=10):
     """64 uneven instances (independent set, set cover, matching) in one arena,
     ``iters`` iterations captured in one CUDA graph with per-instance FP64
@@ -440,6 +481,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = _batched_measurement(args, solver, torch)
+    matching_adjoint = None if args.no_adjoint else _matching_adjoint_measurement(solver, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -459,7 +501,7 @@ def run_ours(args):
                             f"{8 * A.num_slots / 1e6:.0f} MB)", "plan_bind_s": round(plan_s, 2),
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roof, "kernel_shares": shares, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-           "adjoint": adjoint, "batched": batched,
+           "adjoint": adjoint, "adjoint_matching": matching_adjoint, "batched": batched,
            "gpu_launches": launches_per_step * args.steps, "lower_bound_after_run": lb_final}
     if rank == 0:
         print(json.dumps(out))
