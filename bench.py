@@ -238,10 +238,36 @@ def _matching_adjoint_measurement(solver, torch, iters=20, ck=10, reps=5):
         if rep > 0:
             f_ms += ev[0].elapsed_time(ev[1]) / reps
             b_ms += ev[1].elapsed_time(ev[2]) / reps
+    # the same step captured once as a CUDA graph and replayed (what a
+    # training loop over fixed shapes would do)
+    def step():
+        lam.copy_(lam0)
+        M.copy_(M0)
+        A.iterate_checkpointed(lam, M, omega, alpha, iters=iters, ckpt_every=ck, workspace=ws)
+        A.lb_seed_into(lam, M, gl, gM)
+        A.backward_checkpointed(omega, alpha, iters, ck, gl, gM, ws, outs)
+
+    lam, M = lam0.clone(), M0.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        graph.replay()
+    ev[1].record()
+    torch.cuda.synchronize()
+    g_ms = ev[0].elapsed_time(ev[1]) / reps
     return {"workload": "matching_quadratic_200", "N_lambda": int(A.stats.sizes.num_lambda),
             "unrolled_iterations": iters, "checkpoint_every": ck, "parameters": "per-slot omega, alpha",
             "forward_ms": f_ms, "backward_ms": b_ms, "fwd_adjoint_ms": f_ms + b_ms,
-            "loss": "lower bound (eq. 3 plus unary term)"}
+            "fwd_adjoint_graph_replay_ms": g_ms, "loss": "lower bound (eq. 3 plus unary term)"}
 
 
 def _batched_measurement(args, solver, torch, iters=50, ck=10):

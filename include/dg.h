@@ -282,7 +282,10 @@ dg_status dg_iterate_checkpointed(dg_arena* arena, void* stream, float* lam, flo
 /* dg_backward from the checkpoints a preceding dg_iterate_checkpointed left
  * in `workspace` (same arena, iters, ckpt_every, omega, alpha, mode and
  * options; the workspace untouched in between): skips the forward pass of
- * dg_backward, results bit-identical to it. */
+ * dg_backward, results bit-identical to it.  Like dg_iterate_checkpointed and
+ * dg_lb_seed it only enqueues stream-ordered work (no host synchronisation,
+ * no allocation), so a training step's forward + seed + adjoint can be
+ * captured into one CUDA graph by stream capture and replayed. */
 dg_status dg_backward_checkpointed(dg_arena* arena, void* stream, const float* omega, const float* alpha,
                                    int32_t mode, int32_t iters, int32_t ckpt_every, const float* g_lam_T,
                                    const float* g_M_T, float* g_lam0, float* g_M0, float* g_omega, float* g_alpha,
