@@ -26,7 +26,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -151,27 +150,6 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_oracle_rate(budget_s: float = 15.0, frames: int = 50):
-    """The FP64 oracle (single-threaded C++) on a 50-frame slice of the
-    tracking workload: arc updates per second over whole iterations."""
-    import oracle
-    prob = workloads.tracking(frames=frames, dets=2000)
-    O = oracle.Oracle(prob)
-    lam, M = O.init_lambda()
-    arcs = 4 * O.num_nodes
-    t0 = time.perf_counter()
-    its = 0
-    while True:
-        lam, M = O.iterate(lam, M, 0.5, None, 1)
-        its += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": arcs * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"tracking {frames} frames x 2000 detections ({O.num_slots} slots, {O.num_nodes} nodes), "
-                      f"{its} iterations in {dt:.1f} s"}
-
-
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -264,10 +242,15 @@ def _matching_adjoint_measurement(solver, torch, iters=20, ck=10, reps=5):
     ev[1].record()
     torch.cuda.synchronize()
     g_ms = ev[0].elapsed_time(ev[1]) / reps
+    # what the oracle leg compares: the inputs (CSR order) and the gradients
+    # of the last replay
+    keep = {"prob": prob, "lam0": A.to_csr(lam0).double().cpu().numpy(), "M0": A.to_csr(M0).double().cpu().numpy(),
+            "omega": A.to_csr(omega).double().cpu().numpy(), "alpha": A.to_csr(alpha).double().cpu().numpy(),
+            "grads": [A.to_csr(o).double().cpu().numpy() for o in outs], "iters": iters}
     return {"workload": "matching_quadratic_200", "N_lambda": int(A.stats.sizes.num_lambda),
             "unrolled_iterations": iters, "checkpoint_every": ck, "parameters": "per-slot omega, alpha",
             "forward_ms": f_ms, "backward_ms": b_ms, "fwd_adjoint_ms": f_ms + b_ms,
-            "fwd_adjoint_graph_replay_ms": g_ms, "loss": "lower bound (eq. 3 plus unary term)"}
+            "fwd_adjoint_graph_replay_ms": g_ms, "loss": "lower bound (eq. 3 plus unary term)"}, keep
 
 
 def _batched_measurement(args, solver, torch, iters=50, ck=10):
@@ -370,10 +353,168 @@ def _batched_measurement(args, solver, torch, iters=50, ck=10):
             "set_cover": int((kinds == 1).sum()), "matching": int((kinds == 2).sum())},
             "N_lambda": int(A.stats.sizes.num_lambda), "iterations": iters,
             "batched_graph_ms": t_batch, "one_instance_per_launch_ms": t_single,
-            "speedup_plain": t_single / t_batch, "max_rel_bound_difference": rel,
+            "speedup_plain": t_single / t_batch, "max_rel_bound_difference_batched_vs_single": rel,
             "batched_fwd_adjoint_ms": t_batch_adj, "batched_fwd_adjoint_graph_replay_ms": t_batch_adj_graph,
             "one_instance_per_launch_fwd_adjoint_ms": t_single_adj,
-            "speedup_fwd_adjoint": t_single_adj / t_batch_adj, "checkpoint_every": ck}
+            "speedup_fwd_adjoint": t_single_adj / t_batch_adj, "checkpoint_every": ck}, \
+        {"prob": prob, "lb": lb_batch, "iters": iters}
+
+
+def _independent_set_measurement(solver, torch, iters=200, reps=5):
+    """Independent set on G(n = 10,000, p = 8/(n-1)) (about 40,000 two-variable
+    rows), plain method, 200 iterations per CUDA-graph replay: arc updates per
+    second.  Arena and state (~3 MB) stay in L2, so the byte rate is an L2
+    rate, not an HBM one."""
+    prob = workloads.independent_set()
+    A = solver.plan(prob).bind()
+    lam0, M0 = A.init_lambda()
+    lam, M = lam0.clone(), M0.clone()
+    lb = torch.zeros(1, dtype=torch.float64, device=A.device)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = A.graph(lam, M, iters=iters, lb_out=lb, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for r in range(reps + 2):
+            lam.copy_(lam0)
+            M.copy_(M0)
+            e0.record(stream)
+            g.replay(stream)
+            e1.record(stream)
+            e1.synchronize()
+            if r >= 2:
+                ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    st = A.stats
+    arcs = 4 * st.sizes.num_nodes * iters
+    return {"workload": "independent_set_10k", "n_vars": int(st.sizes.n), "constraints": int(st.sizes.m),
+            "N_lambda": int(st.sizes.num_lambda), "N_v": int(st.sizes.num_nodes), "iterations": iters,
+            "value": arcs / (t * 1e-3), "unit": UNIT, "ms_per_iteration": t / iters,
+            "algorithmic_bytes_per_iteration": st.bytes_per_iter,
+            "algorithmic_GBps": st.bytes_per_iter * iters / (t * 1e-3) / 1e9,
+            "memory_level": "L2 (arena + state below the 126 MB L2; not an HBM roofline)",
+            "timing": "median of 5 CUDA-graph replays of 200 iterations"}, \
+        {"prob": prob, "lb": float(lb[0]), "iters": iters}
+
+
+def _err_stats(g, w):
+    rel = float(np.linalg.norm(g - w) / max(1e-12, np.linalg.norm(w)))
+    return {"rel_l2": rel, "frac_within_1e-4": float(np.mean(np.abs(g - w) <= 1e-4)),
+            "max_abs": float(np.abs(g - w).max())}
+
+
+def _oracle_leg(args, A, prob, solver, torch, keep):
+    """The CPU-baseline leg: the FP64 oracle timed on the host (single thread
+    as the checker, and its OpenMP build on all cores), and every figure of
+    the GPU run compared with the oracle on the same seeded inputs.  Nothing
+    here is timed on the GPU."""
+    import oracle
+    par = {"tolerances": {"lambda_M_after_1_iteration": "max abs <= 1e-5 * max|c|",
+                          "bound": "relative <= 1e-5",
+                          "gradients": "rel. L2 < 1e-3 and >= 99% within 1e-4 (long unrolls)"}}
+    # (a) the benchmark instance itself, one iteration from the initial split
+    cmax = float(np.abs(prob["c"]).max())
+    lam, M = A.init_lambda()
+    lb1 = float(A.iterate(lam, M, iters=1, lb=True)[0])
+    t0 = time.perf_counter()
+    O = oracle.Oracle(prob)
+    ol, oM = O.init_lambda()
+    ol, oM = O.iterate(ol, oM, 0.5, None, 1)
+    olb1 = O.lower_bound(ol, oM)
+    el = float(np.abs(A.to_csr(lam).double().cpu().numpy() - ol).max())
+    eM = float(np.abs(A.to_csr(M).double().cpu().numpy() - oM).max())
+    par[args.workload] = {"lambda_max_abs_err_over_max_c": el / cmax, "M_max_abs_err_over_max_c": eM / cmax,
+                          "bound_after_1_iteration": lb1, "bound_rel_err": abs(lb1 - olb1) / max(1.0, abs(olb1)),
+                          "iterations": 1, "oracle_s": time.perf_counter() - t0}
+    del O, ol, oM
+    # (b) 50-frame slice of the same generator: bound after 100 iterations;
+    #     the single-threaded oracle's run is the CPU baseline
+    frames, its = 50, 100
+    sl = workloads.tracking(frames=frames, dets=2000)
+    B = solver.plan(sl).bind()
+    bl, bM = B.init_lambda()
+    glb = float(B.iterate(bl, bM, iters=its, lb=True)[0])
+    O = oracle.Oracle(sl)
+    ol0, oM0 = O.init_lambda()
+    t0 = time.perf_counter()
+    ol, oM = O.iterate(ol0, oM0, 0.5, None, its)
+    dt = time.perf_counter() - t0
+    olb = O.lower_bound(ol, oM)
+    arcs = 4 * O.num_nodes
+    sample = f"tracking {frames} frames x 2000 detections ({O.num_slots} slots, {O.num_nodes} nodes), {its} iterations"
+    cpu = {"value": arcs * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"{sample} in {dt:.1f} s"}
+    par["tracking_50x2000_slice"] = {"bound_after_100_iterations": glb, "bound_rel_err": abs(glb - olb) / abs(olb),
+                                     "iterations": its}
+    cpu_all = None
+    try:
+        P = oracle.Oracle(sl, openmp=True)
+        t0 = time.perf_counter()
+        pl, pM = P.iterate(ol0, oM0, 0.5, None, its)
+        dta = time.perf_counter() - t0
+        cpu_all = {"value": arcs * its / dta, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle (OpenMP over BDDs)",
+                   "sample": f"{sample} in {dta:.1f} s", "bit_identical_to_single_thread":
+                       bool(np.array_equal(pl, ol) and np.array_equal(pM, oM))}
+        del P
+    except Exception as e:  # noqa: BLE001 -- no OpenMP runtime: report why
+        cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
+    del O
+    # (c) the 64-instance batch: per-instance bounds of the timed replay
+    if "batched" in keep:
+        kb = keep["batched"]
+        O = oracle.Oracle(kb["prob"])
+        ol, oM = O.init_lambda()
+        ol, oM = O.iterate(ol, oM, 0.5, None, kb["iters"])
+        want = O.lower_bound(ol, oM, per_instance=True)[1]
+        rel = np.abs(kb["lb"] - want) / np.maximum(1.0, np.abs(want))
+        par["batched_64"] = {"max_bound_rel_err": float(rel.max()), "iterations": kb["iters"]}
+        del O
+    # (d) the independent-set line
+    if "independent_set" in keep:
+        ki = keep["independent_set"]
+        O = oracle.Oracle(ki["prob"])
+        ol, oM = O.init_lambda()
+        ol, oM = O.iterate(ol, oM, 0.5, None, ki["iters"])
+        w = O.lower_bound(ol, oM)
+        par["independent_set_10k"] = {"bound_rel_err": abs(ki["lb"] - w) / max(1.0, abs(w)),
+                                      "iterations": ki["iters"]}
+    # (e) the matching adjoint: gradients against the oracle's Alg. 2, and the
+    #     oracle's own forward + adjoint time on one core
+    cpu_matching = None
+    if "matching" in keep:
+        km = keep["matching"]
+        O = oracle.Oracle(km["prob"])
+        t0 = time.perf_counter()
+        lT, MT = O.iterate(km["lam0"], km["M0"], km["omega"], km["alpha"], km["iters"])
+        sl_, sM_ = O.lb_seed(lT, MT)
+        want = O.backward(km["lam0"], km["M0"], km["omega"], km["alpha"], km["iters"], sl_, sM_)
+        dtm = time.perf_counter() - t0
+        par["adjoint_matching"] = {nm: _err_stats(g, w) for nm, g, w in
+                                   zip(("g_lambda0", "g_M0", "g_omega", "g_alpha"), km["grads"], want)}
+        cpu_matching = {"fwd_adjoint_ms": dtm * 1e3, "cores": 1, "kind": "oracle",
+                        "sample": f"matching_quadratic_200, {km['iters']} unrolled iterations, forward + Alg. 2"}
+    # (f) the tracking adjoint: the full instance's 100-iteration adjoint is
+    #     beyond the oracle's memory (it keeps every sweep); a 12 x 300 slice
+    #     with the same checkpointing (two segments) stands for it
+    if "adjoint" in keep:
+        tr = workloads.tracking(frames=12, dets=300, seed=77)
+        C = solver.plan(tr).bind()
+        T, ck = 10, 5
+        l0, m0 = C.init_lambda()
+        lw, mw = l0.clone(), m0.clone()
+        wsb, _ = C.iterate_checkpointed(lw, mw, iters=T, ckpt_every=ck)
+        gl, gM = C.lb_seed(lw, mw)
+        outs = C.backward_checkpointed(None, None, T, ck, gl, gM, wsb)
+        O = oracle.Oracle(tr)
+        ol, oM = O.init_lambda()
+        ol = np.float32(ol).astype(np.float64)
+        lT, MT = O.iterate(ol, oM, 0.5, None, T)
+        s1, s2 = O.lb_seed(lT, MT)
+        want = O.backward(ol, oM, 0.5, None, T, s1, s2)
+        par["adjoint_tracking_12x300_slice"] = {
+            nm: _err_stats(C.to_csr(g).double().cpu().numpy(), w)
+            for nm, g, w in zip(("g_lambda0", "g_M0"), outs[:2], want[:2])}
+        par["adjoint_tracking_12x300_slice"].update({"unrolled_iterations": T, "checkpoint_every": ck})
+    return cpu, cpu_all, cpu_matching, par
 
 
 def run_ours(args):
@@ -449,7 +590,6 @@ def run_ours(args):
 
     value, total_ms = aggregate(total_ms, arcs_per_iter * args.steps, ws, _max if ws > 1 else None)
     ms_per_step = total_ms / args.steps
-    lb_final = float(lb_out.sum())
 
     # roofline of the dominant kernel (the sweep; forward and backward have
     # the same algorithmic bytes): 16 B per node + 16 B per slot per sweep
@@ -533,14 +673,24 @@ def run_ours(args):
                    "loss": "lower bound (eq. 3 plus unary term)"}
         del wsb
 
+    keep = {}
+    if adjoint is not None:
+        keep["adjoint"] = True
     batched = None
     if not args.no_batched:
-        batched = _batched_measurement(args, solver, torch)
-    matching_adjoint = None if args.no_adjoint else _matching_adjoint_measurement(solver, torch)
+        batched, keep["batched"] = _batched_measurement(args, solver, torch)
+    matching_adjoint = None
+    if not args.no_adjoint:
+        matching_adjoint, keep["matching"] = _matching_adjoint_measurement(solver, torch)
+    independent_set = None
+    if not args.no_is:
+        independent_set, keep["independent_set"] = _independent_set_measurement(solver, torch)
 
-    cpu = None
+    cpu = cpu_all = parity = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = _cpu_oracle_rate(args.cpu_budget)
+        cpu, cpu_all, cpu_matching, parity = _oracle_leg(args, A, prob, solver, torch, keep)
+        if matching_adjoint is not None and cpu_matching is not None:
+            matching_adjoint["cpu_oracle"] = cpu_matching
 
     # 2 sweeps x launch groups, 2 S reductions, lb partial, lb final
     launches_per_step = 2 * int(st.sizes.num_launch_groups) + 4
@@ -556,8 +706,10 @@ def run_ours(args):
                             f"{8 * A.num_slots / 1e6:.0f} MB)", "plan_bind_s": round(plan_s, 2),
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roof, "kernel_shares": shares, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+           "cpu_baseline_all_cores": cpu_all, "parity": parity,
            "adjoint": adjoint, "adjoint_matching": matching_adjoint, "batched": batched,
-           "gpu_launches": launches_per_step * args.steps, "lower_bound_after_run": lb_final}
+           "independent_set_10k": independent_set,
+           "gpu_launches": launches_per_step * args.steps}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -580,8 +732,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-is", action="store_true")
     ap.add_argument("--adjoint-iters", type=int, default=100)
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

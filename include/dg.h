@@ -238,7 +238,9 @@ dg_status dg_lower_bound(dg_arena* arena, void* stream, const float* lam, const 
  * holds the array until exit; all calls share it, so calls that overlap on
  * the GPU race (calls ordered on one stream are safe).  The first call on a
  * device looks up the array's device address; make it before any stream
- * capture. */
+ * capture.  That address is kept for the life of the process: after
+ * cudaDeviceReset (which destroys the context the array lived in) this entry
+ * point must not be called again in the same process. */
 dg_status dg_lower_bound_noalloc(dg_arena* arena, void* stream, const float* lam, const float* M,
                                  double* lb_per_inst);
 

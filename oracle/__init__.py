@@ -19,25 +19,34 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liboracle.so")
+# The same source built with -fopenmp: its sweeps run the (independent) BDDs
+# of a sweep on all host cores.  Used only to time the oracle on every core;
+# the checker is the single-threaded build.
+_SO_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
     """Compiles the oracle with g++ (plain -O2, no architecture flags)."""
     src = os.path.join(_HERE, "dg_oracle.cpp")
-    os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, src])
-        os.replace(tmp, _SO)
-    return _SO
+    so = _SO_OMP if openmp else _SO
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".tmp{os.getpid()}"
+        extra = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["g++", "-O2", "-std=c++17", *extra, "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, so)
+    return so
 
 
-def _load():
-    global _lib
-    if _lib is not None:
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp and _lib_omp is not None:
+        return _lib_omp
+    if not openmp and _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    lib = ctypes.CDLL(build(openmp=openmp))
     P = ctypes.c_void_p
     dp = ctypes.POINTER(ctypes.c_double)
     i64 = ctypes.c_int64
@@ -66,7 +75,10 @@ def _load():
     lib.orc_param_transform_backward.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.orc_smoothed.argtypes = [P, P, ctypes.c_double, P, P]
     lib.orc_last_error.restype = ctypes.c_char_p
-    _lib = lib
+    if openmp:
+        _lib_omp = lib
+    else:
+        _lib = lib
     del dp
     return lib
 
@@ -89,8 +101,9 @@ class Oracle:
     ``inst_var_ptr``).  State vectors are float64 arrays in CSR slot order.
     """
 
-    def __init__(self, rows: dict):
-        lib = _load()
+    def __init__(self, rows: dict, openmp: bool = False):
+        lib = _load(openmp)
+        self._lib = lib
         self._keep = {
             "row_ptr": np.ascontiguousarray(rows["row_ptr"], dtype=np.int64),
             "col": np.ascontiguousarray(rows["col"], dtype=np.int32),
@@ -123,26 +136,26 @@ class Oracle:
         self.deg = np.bincount(self.col, minlength=self.n)
 
     def __del__(self):
-        if getattr(self, "_h", None) is not None and _lib is not None:
-            _lib.orc_destroy(self._h)
+        if getattr(self, "_h", None) is not None and getattr(self, "_lib", None) is not None:
+            self._lib.orc_destroy(self._h)
             self._h = None
 
     # -- structure -------------------------------------------------------
     def bdd(self, j: int):
         """(level_start, lo, hi) of row j; children are ranks on the next level, -2 bottom, -1 top."""
-        nn = _lib.orc_bdd_size(self._h, j)
+        nn = self._lib.orc_bdd_size(self._h, j)
         k = int(self.row_ptr[j + 1] - self.row_ptr[j])
         ls = np.zeros(k + 1, np.int32)
         lo = np.zeros(nn, np.int32)
         hi = np.zeros(nn, np.int32)
-        _lib.orc_bdd_export(self._h, j, _p(ls), _p(lo), _p(hi))
+        self._lib.orc_bdd_export(self._h, j, _p(ls), _p(lo), _p(hi))
         return ls, lo, hi
 
     # -- method ----------------------------------------------------------
     def init_lambda(self):
         lam = np.zeros(self.num_slots)
         M = np.zeros(self.num_slots)
-        _lib.orc_init_lambda(self._h, _p(lam), _p(M))
+        self._lib.orc_init_lambda(self._h, _p(lam), _p(M))
         return lam, M
 
     def _params(self, omega, alpha):
@@ -159,21 +172,21 @@ class Oracle:
         M = np.array(M, dtype=np.float64)
         omega, alpha = self._params(omega, alpha)
         tr = np.zeros(max(iters, 1)) if trace else None
-        _lib.orc_iterate(self._h, _p(lam), _p(M), _p(omega), _p(alpha), int(iters), _p(tr))
+        self._lib.orc_iterate(self._h, _p(lam), _p(M), _p(omega), _p(alpha), int(iters), _p(tr))
         return (lam, M, tr[:iters]) if trace else (lam, M)
 
     def sweep(self, lam, M, forward: bool, omega=0.5, alpha=None):
         lam = np.array(lam, dtype=np.float64)
         M = np.array(M, dtype=np.float64)
         omega, alpha = self._params(omega, alpha)
-        _lib.orc_sweep(self._h, 1 if forward else 0, _p(lam), _p(M), _p(omega), _p(alpha))
+        self._lib.orc_sweep(self._h, 1 if forward else 0, _p(lam), _p(M), _p(omega), _p(alpha))
         return lam, M
 
     def min_marginals(self, lam):
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         m0 = np.zeros(self.num_slots)
         m1 = np.zeros(self.num_slots)
-        _lib.orc_min_marginals(self._h, _p(lam), _p(m0), _p(m1))
+        self._lib.orc_min_marginals(self._h, _p(lam), _p(m0), _p(m1))
         return m0, m1
 
     def lower_bound(self, lam, M, per_instance=False, energies=False):
@@ -181,7 +194,7 @@ class Oracle:
         M = np.ascontiguousarray(M, dtype=np.float64)
         pi = np.zeros(self.num_inst)
         E = np.zeros(self.m) if energies else None
-        tot = _lib.orc_lower_bound(self._h, _p(lam), _p(M), _p(pi), _p(E))
+        tot = self._lib.orc_lower_bound(self._h, _p(lam), _p(M), _p(pi), _p(E))
         out = [tot]
         if per_instance:
             out.append(pi)
@@ -194,33 +207,33 @@ class Oracle:
         M = np.ascontiguousarray(M, dtype=np.float64)
         gl = np.zeros(self.num_slots)
         gM = np.zeros(self.num_slots)
-        _lib.orc_lb_seed(self._h, _p(lam), _p(M), _p(gl), _p(gM))
+        self._lib.orc_lb_seed(self._h, _p(lam), _p(M), _p(gl), _p(gM))
         return gl, gM
 
     def minimiser(self, j: int, lam_row, h: int, beta: int):
         lam_row = np.ascontiguousarray(lam_row, dtype=np.float64)
         x = np.zeros(len(lam_row), np.int32)
-        _lib.orc_minimiser(self._h, int(j), _p(lam_row), int(h), int(beta), _p(x))
+        self._lib.orc_minimiser(self._h, int(j), _p(lam_row), int(h), int(beta), _p(x))
         return x
 
     def nonparam_update(self, lam, theta):
         """eq. 2 on a copy of lam."""
         lam = np.array(lam, dtype=np.float64)
         theta = np.ascontiguousarray(theta, dtype=np.float64)
-        _lib.orc_nonparam_update(self._h, _p(lam), _p(theta))
+        self._lib.orc_nonparam_update(self._h, _p(lam), _p(theta))
         return lam
 
     def param_transform(self, alpha_hat, omega_hat, theta_hat):
         """Alg. 3 output transforms; returns (alpha, omega, theta)."""
         ins = [np.ascontiguousarray(x, dtype=np.float64) for x in (alpha_hat, omega_hat, theta_hat)]
         outs = [np.zeros(self.num_slots) for _ in range(3)]
-        _lib.orc_param_transform(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
+        self._lib.orc_param_transform(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
         return tuple(outs)
 
     def param_transform_backward(self, alpha, omega, g_alpha, g_omega, g_theta):
         ins = [np.ascontiguousarray(x, dtype=np.float64) for x in (alpha, omega, g_alpha, g_omega, g_theta)]
         outs = [np.zeros(self.num_slots) for _ in range(3)]
-        _lib.orc_param_transform_backward(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
+        self._lib.orc_param_transform_backward(self._h, *[_p(x) for x in ins], *[_p(o) for o in outs])
         return tuple(outs)
 
     def smoothed(self, lam, a):
@@ -228,7 +241,7 @@ class Oracle:
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         E = np.zeros(self.m)
         mg = np.zeros(self.num_slots)
-        _lib.orc_smoothed(self._h, _p(lam), float(a), _p(E), _p(mg))
+        self._lib.orc_smoothed(self._h, _p(lam), float(a), _p(E), _p(mg))
         return E, mg
 
     def backward(self, lam0, M0, omega, alpha, iters, g_lamT, g_MT):
@@ -239,6 +252,6 @@ class Oracle:
         g_lamT = np.ascontiguousarray(g_lamT, dtype=np.float64)
         g_MT = np.ascontiguousarray(g_MT, dtype=np.float64)
         outs = [np.zeros(self.num_slots) for _ in range(4)]
-        _lib.orc_backward(self._h, _p(lam0), _p(M0), _p(omega), _p(alpha), int(iters), _p(g_lamT), _p(g_MT),
+        self._lib.orc_backward(self._h, _p(lam0), _p(M0), _p(omega), _p(alpha), int(iters), _p(g_lamT), _p(g_MT),
                           *[_p(o) for o in outs])
         return tuple(outs)

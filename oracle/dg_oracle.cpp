@@ -268,6 +268,9 @@ void sweep(const Problem& P, bool forward, double* lam, double* M, const double*
            const double* alpha, std::vector<std::vector<double>>& d,
            std::vector<std::vector<double>>& t) {
     std::vector<double> S = snapshot_S(P, M);
+    // BDDs are independent within a sweep (reading R1); the pragma only acts
+    // in the separately built all-cores timing copy of this file
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t j = 0; j < P.m; ++j) {
         const Bdd& B = P.bdd[j];
         const int64_t base = P.row_ptr[j];
@@ -320,6 +323,7 @@ double lower_bound_impl(const Problem& P, const double* lam, const double* M, do
 void full_iterate(const Problem& P, double* lam, double* M, const double* omega, const double* alpha,
                   int iters, double* lb_trace) {
     std::vector<std::vector<double>> d(P.m), t(P.m);
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t j = 0; j < P.m; ++j) cost_to_top(P.bdd[j], lam + P.row_ptr[j], t[j]);
     for (int it = 0; it < iters; ++it) {
         sweep(P, true, lam, M, omega, alpha, d, t);

@@ -21,7 +21,10 @@
 //    intermediate it later reads, so nothing needs to start at zero.
 //  * the first call on a device looks up the array's device address (host
 //    code only sees a stand-in for it) with that device current; make that
-//    first call before any stream capture.
+//    first call before any stream capture.  The address is cached per device
+//    ordinal for the life of the process, so a cudaDeviceReset (which
+//    destroys the context holding the array) leaves the cache stale: do not
+//    call this entry point after resetting the device.
 #include <mutex>
 #include <string>
 

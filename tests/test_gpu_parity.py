@@ -116,7 +116,7 @@ def test_config5_full_size_sampled():
         tot = torch.zeros(n, dtype=torch.float64, device=A.device)
         tot.index_add_(0, col, (A.to_csr(lam) + A.to_csr(M)).double())
         resid = (tot - c)[covered].abs().max().item()
-        assert resid <= 1e-4 * float(c.abs().max())
+        assert resid <= TOL_LAM * float(c.abs().max())
     m0, m1 = A.min_marginals(lam)
     lam_csr, m0c, m1c = _np(A.to_csr(lam)), _np(A.to_csr(m0)), _np(A.to_csr(m1))
     rng = np.random.default_rng(0)
