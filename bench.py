@@ -397,6 +397,63 @@ def _independent_set_measurement(solver, torch, iters=200, reps=5):
         {"prob": prob, "lb": float(lb[0]), "iters": iters}
 
 
+def _long_rows_measurement(solver, torch, iters=50, reps=3):
+    """Sparse assignment with long rows (2,000 x 2,000, 300 candidates per
+    left node: 4,000 rows of about 300 variables, every BDD beyond a tile
+    lane): the one-warp-per-BDD sweeps.  Arc updates per second over a
+    CUDA-graph replay of 50 iterations, and the roofline of the long-BDD
+    sweep kernel from its own CUDA-event time."""
+    prob = workloads.assignment()
+    A = solver.plan(prob).bind()
+    st = A.stats
+    lam0, M0 = A.init_lambda()
+    lam, M = lam0.clone(), M0.clone()
+    lb = torch.zeros(1, dtype=torch.float64, device=A.device)
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        g = A.graph(lam, M, iters=iters, lb_out=lb, stream=stream)
+        ms = []
+        for r in range(reps + 1):
+            lam.copy_(lam0)
+            M.copy_(M0)
+            ev[0].record(stream)
+            g.replay(stream)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            if r > 0:
+                ms.append(ev[0].elapsed_time(ev[1]))
+        # one forward and one backward sweep timed on their own
+        sw = []
+        for r in range(4):
+            ev[0].record(stream)
+            A.sweep(lam, M, forward=True, stream=stream)
+            ev[1].record(stream)
+            A.sum_M(M, stream=stream)
+            ev[2].record(stream)
+            A.sweep(lam, M, forward=False, stream=stream)
+            ev[3].record(stream)
+            ev[3].synchronize()
+            if r > 0:
+                sw += [ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])]
+    t = statistics.median(ms)
+    sweep_ms = statistics.mean(sw)
+    Nv, Nl = st.sizes.num_nodes, st.sizes.num_lambda
+    sweep_bytes = 16.0 * Nv + 16.0 * Nl
+    peak, peak_src = _peaks()
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    return {"workload": "assignment_2000x300", "n_vars": int(st.sizes.n), "constraints": int(st.sizes.m),
+            "N_lambda": int(Nl), "N_v": int(Nv), "long_bdds": int(st.sizes.num_long_bdds),
+            "long_nodes": int(st.sizes.num_long_nodes), "iterations": iters,
+            "value": 4 * Nv * iters / (t * 1e-3), "unit": UNIT, "ms_per_iteration": t / iters,
+            "roofline": {"bound": "hbm", "kernel": "k_long_sweep (forward and backward)",
+                         "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": sweep_ms,
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src},
+            "timing": "median of 3 CUDA-graph replays of 50 iterations; sweeps: mean of 3 forward + 3 backward"}, \
+        {"iters": iters}
+
+
 def _err_stats(g, w):
     rel = float(np.linalg.norm(g - w) / max(1e-12, np.linalg.norm(w)))
     return {"rel_l2": rel, "frac_within_1e-4": float(np.mean(np.abs(g - w) <= 1e-4)),
@@ -477,6 +534,27 @@ def _oracle_leg(args, A, prob, solver, torch, keep):
         w = O.lower_bound(ol, oM)
         par["independent_set_10k"] = {"bound_rel_err": abs(ki["lb"] - w) / max(1.0, abs(w)),
                                       "iterations": ki["iters"]}
+    # (d2) the long-row line: the oracle's builder needs ~40 s for the 4,000
+    #      rows of 300 variables, so a 600 x 600 slice of the same generator
+    #      (1,200 rows of about 300 variables) stands for it: lambda after one
+    #      iteration and the bound after the line's 50
+    if "long_rows" in keep:
+        its = keep["long_rows"]["iters"]
+        sl = workloads.assignment(L=600, R=600, cand=300)
+        B = solver.plan(sl).bind()
+        bl, bM = B.init_lambda()
+        B.iterate(bl, bM, iters=1)
+        l1 = B.to_csr(bl).double().cpu().numpy()
+        glb = float(B.iterate(bl, bM, iters=its - 1, lb=True)[0])
+        O = oracle.Oracle(sl)
+        ol, oM = O.init_lambda()
+        ol, oM = O.iterate(ol, oM, 0.5, None, 1)
+        el = float(np.abs(l1 - ol).max()) / float(np.abs(sl["c"]).max())
+        ol, oM = O.iterate(ol, oM, 0.5, None, its - 1)
+        w = O.lower_bound(ol, oM)
+        par["assignment_600x300_slice"] = {"lambda_max_abs_err_over_max_c": el, "bound_rel_err": abs(glb - w) / abs(w),
+                                           "iterations": its}
+        del O, B
     # (e) the matching adjoint: gradients against the oracle's Alg. 2, and the
     #     oracle's own forward + adjoint time on one core
     cpu_matching = None
@@ -642,36 +720,47 @@ def run_ours(args):
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 8 * A.num_inst,
                "ms_per_step": e_ms / ke, "steps": ke}
 
-    # fwd + adjoint of an unrolled solve (Alg. 1 forward, Alg. 2 backward with
-    # a checkpoint every 10 iterations) on the same instance
+    # fwd + adjoint of an unrolled solve (Alg. 1 forward, Alg. 2 backward) on
+    # the same instance: with a checkpoint every 10 iterations (segments
+    # recomputed as recording sweeps; the forward records the last one), and
+    # with one segment (the forward records every sweep: the argmin records
+    # of all 2T sweeps stay in HBM and nothing is recomputed)
     adjoint = None
     if not args.no_adjoint:
-        T, ck = args.adjoint_iters, 10
+        T = args.adjoint_iters
         lam0, M0 = A.init_lambda()
-        ws_bytes = A.backward_workspace_bytes(T, ck)
-        wsb = torch.empty(ws_bytes, dtype=torch.uint8, device=A.device)
         gl = torch.empty_like(lam0)
         gM = torch.empty_like(M0)
-        outs = [torch.empty_like(lam0) for _ in range(4)]
         lamw, Mw = lam0.clone(), M0.clone()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        for rep in range(2):  # first repetition warms up
-            lamw.copy_(lam0)
-            Mw.copy_(M0)
-            torch.cuda.synchronize()
-            ev[0].record(stream)
-            # forward keeping the checkpoints, loss seed, Alg. 2 from the checkpoints
-            A.iterate_checkpointed(lamw, Mw, iters=T, ckpt_every=ck, workspace=wsb)
-            A.lb_seed_into(lamw, Mw, gl, gM)
-            ev[1].record(stream)
-            A.backward_checkpointed(None, None, T, ck, gl, gM, wsb, outs)
-            ev[2].record(stream)
-            torch.cuda.synchronize()
-        f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-        adjoint = {"unrolled_iterations": T, "checkpoint_every": ck, "forward_ms": f_ms, "backward_ms": b_ms,
-                   "fwd_adjoint_ms_per_unrolled_step": (f_ms + b_ms) / T, "workspace_bytes": ws_bytes,
-                   "loss": "lower bound (eq. 3 plus unary term)"}
-        del wsb
+        runs = {}
+        for ck in (10, T):
+            ws_bytes = A.backward_workspace_bytes(T, ck)
+            wsb = torch.empty(ws_bytes, dtype=torch.uint8, device=A.device)
+            outs = [torch.empty_like(lam0) for _ in range(4)]
+            for rep in range(2):  # first repetition warms up
+                lamw.copy_(lam0)
+                Mw.copy_(M0)
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                # forward keeping the checkpoints, loss seed, Alg. 2 from the checkpoints
+                A.iterate_checkpointed(lamw, Mw, iters=T, ckpt_every=ck, workspace=wsb)
+                A.lb_seed_into(lamw, Mw, gl, gM)
+                ev[1].record(stream)
+                A.backward_checkpointed(None, None, T, ck, gl, gM, wsb, outs)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+            f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+            runs[ck] = ({"unrolled_iterations": T, "checkpoint_every": ck, "forward_ms": f_ms, "backward_ms": b_ms,
+                         "backward_ms_per_unrolled_iteration": b_ms / T,
+                         "fwd_adjoint_ms_per_unrolled_step": (f_ms + b_ms) / T, "workspace_bytes": ws_bytes,
+                         "loss": "lower bound (eq. 3 plus unary term)"}, outs)
+            del wsb
+        adjoint = runs[10][0]
+        adjoint["records_in_hbm"] = runs[T][0]
+        adjoint["records_in_hbm"]["gradients_bit_identical_to_checkpoint_10"] = bool(
+            all(torch.equal(x, y) for x, y in zip(runs[10][1], runs[T][1])))
+        del runs
 
     keep = {}
     if adjoint is not None:
@@ -685,6 +774,9 @@ def run_ours(args):
     independent_set = None
     if not args.no_is:
         independent_set, keep["independent_set"] = _independent_set_measurement(solver, torch)
+    long_rows = None
+    if not args.no_long:
+        long_rows, keep["long_rows"] = _long_rows_measurement(solver, torch)
 
     cpu = cpu_all = parity = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -708,7 +800,7 @@ def run_ours(args):
            "roofline": roof, "kernel_shares": shares, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
            "cpu_baseline_all_cores": cpu_all, "parity": parity,
            "adjoint": adjoint, "adjoint_matching": matching_adjoint, "batched": batched,
-           "independent_set_10k": independent_set,
+           "independent_set_10k": independent_set, "long_rows": long_rows,
            "gpu_launches": launches_per_step * args.steps}
     if rank == 0:
         print(json.dumps(out))
@@ -733,6 +825,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-is", action="store_true")
+    ap.add_argument("--no-long", action="store_true")
     ap.add_argument("--adjoint-iters", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

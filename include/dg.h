@@ -109,6 +109,10 @@ typedef struct dg_sizes {
   size_t smem_bytes;     /* shared memory of the largest tile (one warp) */
   int32_t num_launch_groups; /* kernel launches per sweep (tiles grouped by
                                 shared-memory footprint) */
+  int64_t num_long_bdds;     /* BDDs beyond the lane-per-BDD tiles (more than 254
+                                nodes or a level wider than 128), swept one warp
+                                per BDD after the tiles' slots */
+  int64_t num_long_nodes;    /* their nodes (included in num_nodes) */
 } dg_sizes;
 
 typedef struct dg_stats {
@@ -231,10 +235,11 @@ dg_status dg_lower_bound(dg_arena* arena, void* stream, const float* lam, const 
  * capture that forbids allocation or an embedder with a fixed device-memory
  * budget.  The paper has no counterpart: this is a deployment variant.  Its
  * intermediates (E^j per row, S_i and S_i/|J_i| per variable, one partial sum
- * per reduction chunk) live in a static device array of 4 MiB inside libdg
- * instead of the arena's scratch area; the call allocates nothing (no
- * cudaMalloc, no allocating library routine).  Arenas needing more than
- * 4 m + 8 n + 8 * chunks <= 4 MiB get DG_EINVAL.  Every GPU that loads libdg
+ * per reduction chunk, SP(., T) per node of the long BDDs) live in a static
+ * device array of 4 MiB inside libdg instead of the arena's scratch area; the
+ * call allocates nothing (no cudaMalloc, no allocating library routine).
+ * Arenas needing more than 4 m + 8 n + 8 * chunks + 4 * (long-BDD nodes)
+ * <= 4 MiB get DG_EINVAL.  Every GPU that loads libdg
  * holds the array until exit; all calls share it, so calls that overlap on
  * the GPU race (calls ordered on one stream are safe).  The first call on a
  * device looks up the array's device address; make it before any stream
@@ -273,8 +278,13 @@ dg_status dg_backward(dg_arena* arena, void* stream, const float* lam0, const fl
 /* dg_iterate(iters) on (lam, M) in place that also leaves in `workspace`
  * (dg_backward_workspace_bytes(iters, ckpt_every) bytes) the checkpoints of
  * (lam, M) dg_backward would otherwise recompute: the state at the start of
- * every ckpt_every-iteration segment.  The final (lam, M) and lb_per_inst
- * (optional, as in dg_iterate) are bit-identical to dg_iterate's.
+ * every ckpt_every-iteration segment.  The last segment runs as recording
+ * sweeps, so its argmin records (and the S snapshot of each of its sweeps)
+ * are in the workspace too and dg_backward_checkpointed does not recompute
+ * it; with ckpt_every >= iters (one segment) nothing is recomputed.  The
+ * final (lam, M) and lb_per_inst (optional, as in dg_iterate) are
+ * bit-identical to dg_iterate's.  The recording sweeps of every launch group
+ * must fit one CTA's shared memory (DG_EINVAL otherwise, as dg_backward).
  * opts->renorm_every must be 0 (the adjoint does not differentiate the FP64
  * re-projection): DG_EINVAL otherwise. */
 dg_status dg_iterate_checkpointed(dg_arena* arena, void* stream, float* lam, float* M, const float* omega,

@@ -41,7 +41,8 @@ class dg_sizes(ctypes.Structure):
     _fields_ = [("arena_bytes", c_size_t), ("num_slots", c_int64), ("num_lambda", c_int64),
                 ("num_nodes", c_int64), ("num_nodes_padded", c_int64), ("n", c_int32), ("m", c_int64),
                 ("num_inst", c_int32), ("num_tiles", c_int32), ("max_hops", c_int32), ("max_width", c_int32),
-                ("smem_bytes", c_size_t), ("num_launch_groups", c_int32)]
+                ("smem_bytes", c_size_t), ("num_launch_groups", c_int32), ("num_long_bdds", c_int64),
+                ("num_long_nodes", c_int64)]
 
 
 class dg_stats(ctypes.Structure):

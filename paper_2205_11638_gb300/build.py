@@ -21,7 +21,8 @@ CU_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xc
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", f"-I{os.path.join(CUDA_HOME, 'include')}",
              f"-I{os.path.join(ROOT, 'include')}"]
 
-SOURCES = ["builder.cpp", "api.cu", "kernels_sweep.cu", "kernels_misc.cu", "kernels_adjoint.cu", "kernels_params.cu", "noalloc.cu"]
+SOURCES = ["builder.cpp", "api.cu", "kernels_sweep.cu", "kernels_misc.cu", "kernels_adjoint.cu", "kernels_long.cu",
+           "kernels_params.cu", "noalloc.cu"]
 HEADERS = ["dg_internal.h", "kernels.h", "sweep.cuh"]
 
 

@@ -103,6 +103,16 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   return check_launch("dg_iterate");
 }
 
+// The recording sweeps keep an argmin record per node on top of the sweep's
+// shared memory; every launch group's tiles must still fit one CTA.
+dg_status check_recording_fits(const dg_arena* ar, int mode, const char* where) {
+  for (const LaunchGroup& g : ar->groups)
+    if ((size_t)(mode ? g.region_bwd1 : g.region_bwd0) + (size_t)g.meta_bytes > ar->cta_smem_cap ||
+        (size_t)(mode ? g.region_bytes : g.region_bytes0) + (size_t)g.meta_bytes > ar->cta_smem_cap)
+      return fail(DG_EINVAL, std::string(where) + ": a tile's recording sweep does not fit one CTA's shared memory");
+  return DG_OK;
+}
+
 // A state vector may be NULL only when the arena has no slots (no rows).
 bool missing(const dg_arena* ar, const void* p) { return p == nullptr && ar->sizes.num_slots > 0; }
 
@@ -195,6 +205,21 @@ dg_status dg_bdd_export(const dg_plan_t* plan, int64_t j, int32_t* level_start, 
   if (!plan) return fail(DG_EINVAL, "dg_bdd_export: null plan");
   const Plan& P = plan->p;
   if (j < 0 || j >= P.sizes.m) return fail(DG_EINVAL, "dg_bdd_export: row out of range");
+  if (P.long_of_row[j] >= 0) {
+    // a long BDD: levels from its level table, child ranks as stored
+    const int b = P.long_of_row[j];
+    const LongBdd& L = P.longs[b];
+    if (num_nodes) *num_nodes = L.nn;
+    if (!level_start || !lo || !hi) return DG_OK;
+    const int32_t* lvl = P.long_lvl.data() + L.lvl_base;
+    for (int h = 0; h <= L.k; ++h) level_start[h] = lvl[h] - 2;
+    const int64_t r0 = P.long_rank_ptr[b];
+    for (int v = 0; v < L.nn; ++v) {
+      lo[v] = P.long_lo[r0 + v];
+      hi[v] = P.long_hi[r0 + v];
+    }
+    return DG_OK;
+  }
   const int64_t nb = P.node_ptr[j], ne = P.node_ptr[j + 1];
   if (num_nodes) *num_nodes = (int32_t)(ne - nb);
   if (!level_start || !lo || !hi) return DG_OK;
@@ -248,6 +273,11 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   cp(P.off.lb_chunks, P.lb_chunks.data(), P.lb_chunks.size() * 4);
   cp(P.off.inst_chunk_ptr, P.inst_chunk_ptr.data(), P.inst_chunk_ptr.size() * 4);
   cp(P.off.inst_unc, P.inst_unc.data(), P.inst_unc.size() * 8);
+  cp(P.off.longs, P.longs.data(), P.longs.size() * sizeof(LongBdd));
+  cp(P.off.long_code, P.long_code.data(), P.long_code.size() * sizeof(int2));
+  cp(P.off.long_lvl, P.long_lvl.data(), P.long_lvl.size() * 4);
+  cp(P.off.long_in_ptr, P.long_in_ptr.data(), P.long_in_ptr.size() * 4);
+  cp(P.off.long_in, P.long_in.data(), P.long_in.size() * 4);
   cudaError_t e = cudaMemcpyAsync(arena_dev, h.data(), image, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)arena_dev + P.off.S, 0, P.off.total - P.off.S, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -299,6 +329,13 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.lb_chunks = (const int4*)(b + P.off.lb_chunks);
   A.inst_chunk_ptr = (const int32_t*)(b + P.off.inst_chunk_ptr);
   A.inst_unc = (const double*)(b + P.off.inst_unc);
+  A.longs = (const LongBdd*)(b + P.off.longs);
+  A.long_code = (const int2*)(b + P.off.long_code);
+  A.long_lvl = (const int32_t*)(b + P.off.long_lvl);
+  A.long_in_ptr = (const int32_t*)(b + P.off.long_in_ptr);
+  A.long_in = (const int32_t*)(b + P.off.long_in);
+  A.long_d = (float*)(b + P.off.long_d);
+  A.long_t = (float*)(b + P.off.long_t);
   A.S = (float*)(b + P.off.S);
   A.Sbar = (float*)(b + P.off.Sbar);
   A.E = (float*)(b + P.off.E);
@@ -309,6 +346,10 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.num_slots = P.sizes.num_slots;
   A.num_tiles = P.sizes.num_tiles;
   A.num_lb_chunks = (int32_t)(P.lb_chunks.size() / 4);
+  A.num_long = (int32_t)P.longs.size();
+  A.long_slot_base = P.long_slot_base;
+  A.long_cost_size = P.long_cost_size;
+  A.long_stream = P.long_stream;
   ar->sizes = P.sizes;
   ar->smem_sweep = P.smem_sweep;
   ar->groups = P.groups;
@@ -327,7 +368,10 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   // write, M write 20 B per slot; alpha and S gathers 8 B per lambda.  Per
   // S reduction: variable CSR and M gather 8 B per lambda, pointers and S 8 B
   // per variable.
-  S.actual_bytes_per_iter = 2.0 * (2.0 * NVp + 20.0 * ns + 8.0 * Nl) + 2.0 * (8.0 * n + 8.0 * Nl);
+  // long BDDs per sweep: children 8 B and in-arcs ~8 B per node, both path
+  // costs read and written 16 B per node
+  S.actual_bytes_per_iter = 2.0 * (2.0 * NVp + 20.0 * ns + 8.0 * Nl) + 2.0 * (8.0 * n + 8.0 * Nl) +
+                            2.0 * 32.0 * (double)P.sizes.num_long_nodes;
   for (int i = 0; i < 64; ++i) S.hop_histogram[i] = P.hop_histogram[i];
   *out = ar;
   return DG_OK;
@@ -454,7 +498,7 @@ dg_status dg_wait(void* stream, int32_t timeout_ms) {
 
 int32_t dg_iterate_launches(const dg_arena* ar, int32_t iters, int32_t want_lb, const dg_options* opts) {
   (void)opts;
-  const int32_t g = ar ? (int32_t)ar->groups.size() : 1;
+  const int32_t g = ar ? (int32_t)ar->groups.size() + (ar->dev.num_long > 0 ? 1 : 0) : 1;
   int32_t l = 1 + iters * (2 * g + 2);
   if (want_lb) l += 2 + (iters == 0 ? g : 0);
   return l;
@@ -647,8 +691,11 @@ void dg_graph_destroy(dg_graph_t* g) {
 namespace {
 
 struct BwdLayout {
-  size_t ck_lam, ck_M, rec_meta, rec_amin, rec_diff, seg_S, w_lam, w_M, sdot, sd_a, sd_b, total;
-  size_t meta_stride;  // bytes of one sweep's node records
+  size_t ck_lam, ck_M, rec_meta, rec_amin, rec_diff, seg_S, w_lam, w_M, sdot, sd_a, sd_b, rec_lmeta, rec_lamin,
+      long_a1, long_a2, total;
+  size_t meta_stride;   // bytes of one sweep's node records
+  size_t lmeta_stride;  // ... of the long BDDs' node records
+  size_t lamin_stride;  // ... of the long BDDs' slot records
   int nseg, k;
 };
 
@@ -676,8 +723,56 @@ BwdLayout backward_layout(const dg_arena* ar, int iters, int ckpt_every) {
   L.sdot = put(NS * 4);
   L.sd_a = put(n * 4);
   L.sd_b = put(n * 4);
+  // long BDDs: node and slot records of every sweep of one segment, and the
+  // per-node gradients of the adjoint
+  const size_t lcost = (size_t)ar->dev.long_cost_size, lslots = NS - (size_t)ar->dev.long_slot_base;
+  L.lmeta_stride = lcost * 4;
+  L.lamin_stride = lslots * 8;
+  L.rec_lmeta = put((size_t)2 * L.k * L.lmeta_stride);
+  L.rec_lamin = put((size_t)2 * L.k * L.lamin_stride);
+  L.long_a1 = put(lcost * 4);
+  L.long_a2 = put(lcost * 4);
   L.total = o;
   return L;
+}
+
+// Runs `k` iterations from (lam, M) as recording sweeps: before sweep sw the
+// S snapshot is taken and kept in seg_S[sw], the sweep's argmin records go to
+// record slot sw of the workspace.  The same kernels in the same order as
+// enqueue_iterate (the recording sweeps compute the same values), so lam, M
+// and the bound are bit-identical to k plain iterations.  With lb_out the last
+// backward sweep writes the energies and the bound follows.
+dg_status enqueue_recorded_segment(dg_arena* ar, cudaStream_t st, float* lam, float* M, const float* omega,
+                                   const float* alpha, int mode, int k, const BwdLayout& L, char* w, double* lb_out,
+                                   const dg_options* opts) {
+  const DevArena& A = ar->dev;
+  const size_t NS = (size_t)ar->sizes.num_slots, n = (size_t)ar->sizes.n;
+  SweepArgs fa{};
+  fa.lam = lam;
+  fa.M = M;
+  fa.omega = omega;
+  fa.alpha = alpha;
+  fa.omega0 = omega_of(opts);
+  fa.mode = mode;
+  cudaError_t e = cudaSuccess;
+  for (int sw = 0; sw < 2 * k; ++sw) {
+    launch_reduce_S(A, M, nullptr, nullptr, mode, false, st);
+    if (e == cudaSuccess && n)
+      e = cudaMemcpyAsync(w + L.seg_S + (size_t)sw * n * 4, A.S, n * 4, cudaMemcpyDeviceToDevice, st);
+    SweepArgs ra = fa;
+    ra.rec_meta = (uint16_t*)(w + L.rec_meta + (size_t)sw * L.meta_stride);
+    ra.rec_amin = (uint16_t*)(w + L.rec_amin) + (size_t)sw * NS;
+    ra.rec_diff = (float*)(w + L.rec_diff) + (size_t)sw * NS;
+    ra.rec_lmeta = (int32_t*)(w + L.rec_lmeta + (size_t)sw * L.lmeta_stride);
+    ra.rec_lamin = (int2*)(w + L.rec_lamin + (size_t)sw * L.lamin_stride);
+    if (lb_out && sw == 2 * k - 1) ra.E = A.E;
+    launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads_of(opts), ar->groups.data(), (int)ar->groups.size(),
+                 streams_for(ar, st));
+  }
+  launch_reduce_S(A, M, nullptr, nullptr, mode, false, st);
+  if (lb_out) launch_lower_bound(A, lb_out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "recorded segment copies");
+  return check_launch("recorded segment");
 }
 
 }  // namespace
@@ -712,10 +807,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   for (const AdjGroup& g : ar->adj_groups)
     if ((size_t)g.region > ar->cta_smem_cap)
       return fail(DG_EINVAL, "dg_backward: a tile's adjoint state does not fit one CTA's shared memory");
-  for (const LaunchGroup& g : ar->groups)
-    if ((size_t)(mode ? g.region_bwd1 : g.region_bwd0) + (size_t)g.meta_bytes > ar->cta_smem_cap ||
-        (size_t)(mode ? g.region_bytes : g.region_bytes0) + (size_t)g.meta_bytes > ar->cta_smem_cap)
-      return fail(DG_EINVAL, "dg_backward: a tile's recording sweep does not fit one CTA's shared memory");
+  if (dg_status s = check_recording_fits(ar, mode, "dg_backward")) return s;
   const BwdLayout L = backward_layout(ar, iters, ckpt_every);
   if (iters > 0 && (!workspace || ws_bytes < L.total))
     return fail(DG_EINVAL, "dg_backward: workspace smaller than dg_backward_workspace_bytes()");
@@ -764,7 +856,14 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   for (int c = 0; c < (have_ckpt ? 0 : L.nseg); ++c) {
     cpy(ck_lam + (size_t)c * NS, w_lam, bNS);
     cpy(ck_M + (size_t)c * NS, w_M, bNS);
-    if (c + 1 == L.nseg) break;
+    if (c + 1 == L.nseg) {
+      // the last segment runs as recording sweeps right away
+      if (e != cudaSuccess) return cuda_fail(e, "dg_backward copies");
+      if (dg_status s = enqueue_recorded_segment(ar, st, w_lam, w_M, omega, alpha, mode, iters - c * L.k, L, w,
+                                                 nullptr, opts))
+        return s;
+      break;
+    }
     for (int it = 0; it < L.k; ++it) {
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
       launch_sweep(kFwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
@@ -773,7 +872,8 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
     }
   }
   // 2. segments newest first: recompute every sweep of the segment as a
-  //    recording sweep (its argmins and S at its start kept), then run the
+  //    recording sweep (its argmins and S at its start kept; the last
+  //    segment's are already there from the forward pass), then run the
   //    adjoint sweeps backwards
   cpy(g_lam0, g_lam_T, bNS);
   AdjArgs aa{};
@@ -785,19 +885,26 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   aa.g_omega = g_omega;
   aa.g_alpha = g_alpha;
   aa.sdot = sdot;
+  aa.long_a1 = (float*)(w + L.long_a1);
+  aa.long_a2 = (float*)(w + L.long_a2);
   const int last_sweep = 2 * iters - 1;
   for (int c = L.nseg - 1; c >= 0; --c) {
     const int it0 = c * L.k, it1 = std::min(iters, it0 + L.k);
     const int nsw = 2 * (it1 - it0);
-    cpy(w_lam, ck_lam + (size_t)c * NS, bNS);
-    cpy(w_M, ck_M + (size_t)c * NS, bNS);
-    for (int sw = 0; sw < nsw; ++sw) {
+    const bool recorded = c + 1 == L.nseg;
+    if (!recorded) {
+      cpy(w_lam, ck_lam + (size_t)c * NS, bNS);
+      cpy(w_M, ck_M + (size_t)c * NS, bNS);
+    }
+    for (int sw = 0; sw < (recorded ? 0 : nsw); ++sw) {
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
       cpy(seg_S + (size_t)sw * n, A.S, bn);
       SweepArgs ra = fa;
       ra.rec_meta = (uint16_t*)(rec_meta + (size_t)sw * L.meta_stride);
       ra.rec_amin = rec_amin + (size_t)sw * NS;
       ra.rec_diff = rec_diff + (size_t)sw * NS;
+      ra.rec_lmeta = (int32_t*)(w + L.rec_lmeta + (size_t)sw * L.lmeta_stride);
+      ra.rec_lamin = (int2*)(w + L.rec_lamin + (size_t)sw * L.lamin_stride);
       launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads, ar->groups.data(), (int)ar->groups.size(),
                    streams_for(ar, st));
     }
@@ -806,6 +913,8 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       aa.rec_meta = (const uint16_t*)(rec_meta + (size_t)sw * L.meta_stride);
       aa.rec_amin = rec_amin + (size_t)sw * NS;
       aa.rec_diff = rec_diff + (size_t)sw * NS;
+      aa.rec_lmeta = (const int32_t*)(w + L.rec_lmeta + (size_t)sw * L.lmeta_stride);
+      aa.rec_lamin = (const int2*)(w + L.rec_lamin + (size_t)sw * L.lamin_stride);
       aa.S_in = seg_S + (size_t)sw * n;
       aa.seed_M = gsw == last_sweep ? g_M_T : nullptr;
       aa.sdot_next = gsw == last_sweep ? nullptr : sd_next;
@@ -855,6 +964,7 @@ dg_status dg_iterate_checkpointed(dg_arena* ar, void* stream, float* lam, float*
   if (opts && opts->block_threads != 0 && (opts->block_threads % 32 != 0 || opts->block_threads > 512))
     return fail(DG_EINVAL, "dg_iterate_checkpointed: block_threads must be a multiple of 32 in [32, 512]");
   if (dg_status s = check_vectors("dg_iterate_checkpointed", lam, M, omega, alpha)) return s;
+  if (dg_status s = check_recording_fits(ar, mode, "dg_iterate_checkpointed")) return s;
   const BwdLayout L = backward_layout(ar, iters, ckpt_every);
   if (iters > 0 && (!workspace || ws_bytes < L.total))
     return fail(DG_EINVAL, "dg_iterate_checkpointed: workspace smaller than dg_backward_workspace_bytes()");
@@ -866,9 +976,13 @@ dg_status dg_iterate_checkpointed(dg_arena* ar, void* stream, float* lam, float*
     if (e == cudaSuccess) e = cudaMemcpyAsync(w + L.ck_M + (size_t)c * bNS, M, bNS, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "dg_iterate_checkpointed copies");
     const int k = std::min(L.k, iters - c * L.k);
-    const bool last = c + 1 == L.nseg;
-    if (dg_status s = enqueue_iterate(ar, st, lam, M, omega, alpha, mode, k, last ? lb_out : nullptr, opts))
+    if (c + 1 == L.nseg) {
+      // the last segment's argmin records stay in the workspace, so that
+      // dg_backward_checkpointed does not recompute that segment
+      if (dg_status s = enqueue_recorded_segment(ar, st, lam, M, omega, alpha, mode, k, L, w, lb_out, opts)) return s;
+    } else if (dg_status s = enqueue_iterate(ar, st, lam, M, omega, alpha, mode, k, nullptr, opts)) {
       return s;
+    }
   }
   if (iters == 0) return enqueue_iterate(ar, st, lam, M, omega, alpha, mode, 0, lb_out, opts);
   return DG_OK;

@@ -31,12 +31,14 @@ struct RowResult {
 
 // Scratch reused across the rows one host thread builds.
 struct RowScratch {
-  std::vector<int64_t> sums;      // reachable partial sums, level by level
+  std::vector<int64_t> sums;      // reachable partial sums (clamped), level by level
+  std::vector<int64_t> rem_lo, rem_hi;  // per level: least / largest sum of the remaining terms
   std::vector<size_t> lvl;        // level offsets into sums
   std::vector<int32_t> code;      // code of every (level, sum)
-  std::vector<uint32_t> keys;     // (lo+2) << 16 | (hi+2) per sum of a level
-  std::vector<uint32_t> uniq;
-  std::vector<int64_t> merged;
+  std::vector<uint64_t> keys;     // (lo+2) << 32 | (hi+2) per sum of a level
+  std::vector<std::vector<uint64_t>> level_keys;  // per level: its nodes' keys, ascending
+  int64_t nodes = 0;
+  int maxw = 0;
 };
 
 inline bool row_holds(int64_t act, int sense, int64_t rhs) {
@@ -47,29 +49,45 @@ inline bool row_holds(int64_t act, int sense, int64_t rhs) {
   }
 }
 
-// Builds the BDD of one row; appends the level widths to `width` and the
-// child ranks of every node to lo/hi.
-RowResult build_row(const int32_t* a, int k, int sense, int64_t rhs, RowScratch& sc, std::vector<uint8_t>& width,
-                    std::vector<int8_t>& lo, std::vector<int8_t>& hi) {
+inline int key_lo(uint64_t key) { return int(key >> 32) - 2; }
+inline int key_hi(uint64_t key) { return int(key & 0xFFFFFFFFu) - 2; }
+
+// Builds the BDD of one row: on success sc.level_keys[h] holds the nodes of
+// level h in canonical order as keys (lo code + 2) << 32 | (hi code + 2),
+// codes being ranks on level h + 1 with bottom = -2 and top = -1.
+RowResult build_row(const int32_t* a, int k, int sense, int64_t rhs, RowScratch& sc) {
   RowResult res;
-  // 1. partial sums reachable from the root, per level (sorted, unique)
+  // 1. partial sums reachable from the root, per level (sorted, unique).  A
+  // partial sum s of level g behaves like any other sum outside the window
+  // [rhs - rem_hi[g] - 1, rhs - rem_lo[g] + 1] on the same side of it (below
+  // it every completion is feasible for '<=' and none for '>=' and '='; above
+  // it the reverse), and adding a term keeps it outside, so sums are clamped
+  // to the window: the same residual functions, hence the same BDD, from
+  // O(k * window) partial sums instead of every reachable one.
+  sc.rem_lo.assign(k + 1, 0);
+  sc.rem_hi.assign(k + 1, 0);
+  for (int h = k - 1; h >= 0; --h) {
+    sc.rem_lo[h] = sc.rem_lo[h + 1] + std::min<int64_t>(0, a[h]);
+    sc.rem_hi[h] = sc.rem_hi[h + 1] + std::max<int64_t>(0, a[h]);
+  }
+  auto clamp = [&](int64_t v, int g) {
+    return std::min(std::max(v, rhs - sc.rem_hi[g] - 1), rhs - sc.rem_lo[g] + 1);
+  };
   sc.sums.clear();
   sc.lvl.assign(1, 0);
-  sc.sums.push_back(0);
+  sc.sums.push_back(clamp(0, 0));
   sc.lvl.push_back(1);
   for (int h = 0; h < k; ++h) {
     size_t b = sc.lvl[h], e = sc.lvl[h + 1];
-    sc.merged.clear();
     size_t p = b, q = b;
-    while (p < e || q < e) {  // merge {s} and {s + a_h}, both ascending
-      int64_t x = p < e ? sc.sums[p] : INT64_MAX;
-      int64_t y = q < e ? sc.sums[q] + a[h] : INT64_MAX;
+    while (p < e || q < e) {  // merge {s} and {s + a_h}, both ascending (clamping is monotone)
+      int64_t x = p < e ? clamp(sc.sums[p], h + 1) : INT64_MAX;
+      int64_t y = q < e ? clamp(sc.sums[q] + a[h], h + 1) : INT64_MAX;
       int64_t v = std::min(x, y);
       if (x == v) ++p;
       if (y == v) ++q;
-      if (sc.merged.empty() || sc.merged.back() != v) sc.merged.push_back(v);
+      if (sc.sums.size() == e || sc.sums.back() != v) sc.sums.push_back(v);
     }
-    sc.sums.insert(sc.sums.end(), sc.merged.begin(), sc.merged.end());
     sc.lvl.push_back(sc.sums.size());
     if (sc.sums.size() > kMaxStatesPerRow) {
       res.status = DG_EINVAL;
@@ -80,10 +98,7 @@ RowResult build_row(const int32_t* a, int k, int sense, int64_t rhs, RowScratch&
   // 2. codes bottom-up
   sc.code.assign(sc.sums.size(), kCodeBot);
   for (size_t q = sc.lvl[k]; q < sc.lvl[k + 1]; ++q) sc.code[q] = row_holds(sc.sums[q], sense, rhs) ? kCodeTop : kCodeBot;
-  const size_t width_base = width.size();
-  width.resize(width_base + k);
-  // level nodes are emitted top-down at the end; remember the unique keys
-  std::vector<std::vector<uint32_t>> level_keys(k);
+  if (sc.level_keys.size() < (size_t)k) sc.level_keys.resize(k);
   for (int h = k - 1; h >= 0; --h) {
     const size_t b = sc.lvl[h], e = sc.lvl[h + 1];
     const size_t nb = sc.lvl[h + 1], ne = sc.lvl[h + 2];
@@ -92,47 +107,41 @@ RowResult build_row(const int32_t* a, int k, int sense, int64_t rhs, RowScratch&
     sc.keys.resize(e - b);
     for (size_t q = b; q < e; ++q) {
       const int64_t s = sc.sums[q];
-      size_t i0 = std::lower_bound(nxt, nxt + nn, s) - nxt;
-      size_t i1 = std::lower_bound(nxt, nxt + nn, s + a[h]) - nxt;
-      int c0 = sc.code[nb + i0], c1 = sc.code[nb + i1];
-      sc.keys[q - b] = (uint32_t(c0 + 2) << 16) | uint32_t(c1 + 2);
+      size_t i0 = std::lower_bound(nxt, nxt + nn, clamp(s, h + 1)) - nxt;
+      size_t i1 = std::lower_bound(nxt, nxt + nn, clamp(s + a[h], h + 1)) - nxt;
+      const int c0 = sc.code[nb + i0], c1 = sc.code[nb + i1];
+      sc.keys[q - b] = (uint64_t(uint32_t(c0 + 2)) << 32) | uint64_t(uint32_t(c1 + 2));
     }
-    sc.uniq.assign(sc.keys.begin(), sc.keys.end());
-    std::sort(sc.uniq.begin(), sc.uniq.end());
-    sc.uniq.erase(std::unique(sc.uniq.begin(), sc.uniq.end()), sc.uniq.end());
-    if (!sc.uniq.empty() && sc.uniq.front() == 0u) sc.uniq.erase(sc.uniq.begin());  // (bottom, bottom)
-    if (sc.uniq.size() > (size_t)kMaxWidth) {
-      res.status = DG_EINVAL;
-      res.msg = "a BDD level has more than 128 nodes (child ranks are 8-bit)";
-      return res;
-    }
+    std::vector<uint64_t>& uniq = sc.level_keys[h];
+    uniq.assign(sc.keys.begin(), sc.keys.end());
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    if (!uniq.empty() && uniq.front() == 0u) uniq.erase(uniq.begin());  // (bottom, bottom)
     for (size_t q = b; q < e; ++q) {
-      uint32_t key = sc.keys[q - b];
-      sc.code[q] = key == 0u ? kCodeBot
-                             : int(std::lower_bound(sc.uniq.begin(), sc.uniq.end(), key) - sc.uniq.begin());
+      const uint64_t key = sc.keys[q - b];
+      sc.code[q] = key == 0u ? kCodeBot : int(std::lower_bound(uniq.begin(), uniq.end(), key) - uniq.begin());
     }
-    level_keys[h] = sc.uniq;
   }
   if (sc.code[0] == kCodeBot) {
     res.status = DG_EINFEASIBLE;
     res.msg = "row has no feasible assignment";
     return res;
   }
+  sc.nodes = 0;
+  sc.maxw = 0;
   for (int h = 0; h < k; ++h) {
     bool zero_ok = false, one_ok = false;
-    for (uint32_t key : level_keys[h]) {
-      int c0 = int(key >> 16) - 2, c1 = int(key & 0xFFFFu) - 2;
-      lo.push_back((int8_t)c0);
-      hi.push_back((int8_t)c1);
-      zero_ok |= c0 != kCodeBot;
-      one_ok |= c1 != kCodeBot;
+    for (uint64_t key : sc.level_keys[h]) {
+      zero_ok |= key_lo(key) != kCodeBot;
+      one_ok |= key_hi(key) != kCodeBot;
     }
-    width[width_base + h] = (uint8_t)level_keys[h].size();
     if (!zero_ok || !one_ok) {
       res.status = DG_EFORCED;
       res.msg = "row fixes one of its variables (presolve it away)";
       return res;
     }
+    sc.nodes += (int64_t)sc.level_keys[h].size();
+    sc.maxw = std::max<int>(sc.maxw, (int)sc.level_keys[h].size());
   }
   return res;
 }
@@ -189,11 +198,14 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
 
   // ---- 1. BDDs, in parallel over contiguous row ranges --------------------
   int nthreads = opts && opts->num_threads > 0 ? opts->num_threads : (int)std::thread::hardware_concurrency();
-  nthreads = std::max(1, std::min<int>(nthreads, (int)std::max<int64_t>(1, m / 4096)));
+  nthreads = std::max(1, std::min<int>(nthreads, (int)std::max<int64_t>(1, std::min<int64_t>(m / 64, nnz / 16384))));
   struct Part {
     std::vector<uint8_t> width;
     std::vector<int8_t> lo, hi;
     std::vector<int32_t> nodes_of_row;
+    // rows whose BDD exceeds the tile limits: row, level widths, child ranks
+    std::vector<int64_t> long_rows;
+    std::vector<int32_t> lwidth, llo, lhi;
     RowResult err;
     int64_t err_row = -1;
   };
@@ -207,14 +219,33 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     for (int64_t j = cut[t]; j < cut[t + 1]; ++j) {
       const int64_t b = R->row_ptr[j];
       const int k = (int)(R->row_ptr[j + 1] - b);
-      size_t before = pt.lo.size();
-      RowResult r = build_row(R->coef + b, k, R->sense[j], R->rhs[j], sc, pt.width, pt.lo, pt.hi);
+      RowResult r = build_row(R->coef + b, k, R->sense[j], R->rhs[j], sc);
       if (r.status != 0) {
         pt.err = r;
         pt.err_row = j;
         return;
       }
-      pt.nodes_of_row.push_back((int32_t)(pt.lo.size() - before));
+      if (sc.nodes <= kMaxNodesPerBdd && sc.maxw <= kMaxWidth) {
+        for (int h = 0; h < k; ++h) {
+          pt.width.push_back((uint8_t)sc.level_keys[h].size());
+          for (uint64_t key : sc.level_keys[h]) {
+            pt.lo.push_back((int8_t)key_lo(key));
+            pt.hi.push_back((int8_t)key_hi(key));
+          }
+        }
+        pt.nodes_of_row.push_back((int32_t)sc.nodes);
+      } else {
+        pt.width.insert(pt.width.end(), (size_t)k, (uint8_t)0);
+        pt.nodes_of_row.push_back(0);
+        pt.long_rows.push_back(j);
+        for (int h = 0; h < k; ++h) {
+          pt.lwidth.push_back((int32_t)sc.level_keys[h].size());
+          for (uint64_t key : sc.level_keys[h]) {
+            pt.llo.push_back(key_lo(key));
+            pt.lhi.push_back(key_hi(key));
+          }
+        }
+      }
     }
   };
   if (nthreads == 1) {
@@ -231,6 +262,8 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   std::vector<uint8_t> width;
   width.reserve(nnz);
   P.node_ptr.assign(m + 1, 0);
+  std::vector<int64_t> long_rows;
+  std::vector<int32_t> long_width;  // level widths of the long BDDs, in row order
   {
     int64_t j = 0;
     for (int t = 0; t < nthreads; ++t) {
@@ -241,13 +274,22 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
         P.node_ptr[j + 1] = P.node_ptr[j] + c;
         ++j;
       }
+      long_rows.insert(long_rows.end(), parts[t].long_rows.begin(), parts[t].long_rows.end());
+      long_width.insert(long_width.end(), parts[t].lwidth.begin(), parts[t].lwidth.end());
+      P.long_lo.insert(P.long_lo.end(), parts[t].llo.begin(), parts[t].llo.end());
+      P.long_hi.insert(P.long_hi.end(), parts[t].lhi.begin(), parts[t].lhi.end());
       std::vector<uint8_t>().swap(parts[t].width);
       std::vector<int8_t>().swap(parts[t].lo);
       std::vector<int8_t>().swap(parts[t].hi);
+      std::vector<int32_t>().swap(parts[t].llo);
+      std::vector<int32_t>().swap(parts[t].lhi);
     }
   }
   P.row_ptr.assign(R->row_ptr, R->row_ptr + m + 1);
-  const int64_t num_nodes = P.node_ptr[m];
+  P.long_of_row.assign(m, -1);
+  for (size_t b = 0; b < long_rows.size(); ++b) P.long_of_row[long_rows[b]] = (int32_t)b;
+  const int64_t num_long_nodes = (int64_t)P.long_lo.size();
+  const int64_t num_nodes = P.node_ptr[m] + num_long_nodes;
 
   // ---- 2. tiles: 32 BDDs per tile, one per lane ---------------------------
   // Rows are cut into chunks of consecutive rows (so that a tile's variables,
@@ -258,9 +300,13 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   // element 32 n + b of the per-tile arrays.  Node numbers 0 and 1 stand for
   // the top and bottom terminals, the BDD's own nodes are numbered 2, 3, ...
   // level by level; child codes are node numbers (8 bits).
+  // Rows of the long BDDs take no tile (they are laid out after the tiles).
   const int64_t kChunkRows = opts && opts->chunk_rows > 0 ? opts->chunk_rows : 16384;
-  std::vector<int64_t> order(m);
-  std::iota(order.begin(), order.end(), 0);
+  std::vector<int64_t> order;
+  order.reserve(m - (int64_t)long_rows.size());
+  for (int64_t j = 0; j < m; ++j)
+    if (P.long_of_row[j] < 0) order.push_back(j);
+  const int64_t m_tiles = (int64_t)order.size();
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
     const int64_t cx = x / kChunkRows, cy = y / kChunkRows;
     if (cx != cy) return cx < cy;
@@ -273,13 +319,11 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
     max_hops = std::max(max_hops, k);
     P.hop_histogram[std::min(k, 63)]++;
-    if (P.node_ptr[j + 1] - P.node_ptr[j] > kMaxNodesPerBdd)
-      return fail(DG_EINVAL, "dg_plan: row " + std::to_string(j) + " has a BDD of more than " +
-                                 std::to_string(kMaxNodesPerBdd) + " nodes");
   }
   for (uint8_t w : width) max_width = std::max<int>(max_width, w);
+  for (int32_t w : long_width) max_width = std::max<int>(max_width, w);
 
-  const int T = (int)((m + kWarp - 1) / kWarp);
+  const int T = (int)((m_tiles + kWarp - 1) / kWarp);
   if (opts && opts->host_mb_limit > 0) {
     // host bytes of the arena image about to be built: child codes, slot
     // arrays (descriptor, variable, row, CSR position), variable CSR and ELL
@@ -294,7 +338,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   // are contiguous (and the longest tiles start first)
   std::vector<int> tile_nh(T, 0), tile_nmax(T, 2), tile_maxw(T, 1), tile_order(T);
   for (int t = 0; t < T; ++t) {
-    for (int64_t q = (int64_t)t * kWarp; q < std::min<int64_t>(m, (int64_t)(t + 1) * kWarp); ++q) {
+    for (int64_t q = (int64_t)t * kWarp; q < std::min<int64_t>(m_tiles, (int64_t)(t + 1) * kWarp); ++q) {
       const int64_t j = order[q];
       tile_nh[t] = std::max<int>(tile_nh[t], (int)(R->row_ptr[j + 1] - R->row_ptr[j]));
       tile_nmax[t] = std::max<int>(tile_nmax[t], 2 + (int)(P.node_ptr[j + 1] - P.node_ptr[j]));
@@ -311,7 +355,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   size_t smem_max = 0, smem_adj_max = 0;
   for (int t = 0; t < T; ++t) {
     const int src = tile_order[t];
-    const int64_t q0 = (int64_t)src * kWarp, q1 = std::min<int64_t>(m, q0 + kWarp);
+    const int64_t q0 = (int64_t)src * kWarp, q1 = std::min<int64_t>(m_tiles, q0 + kWarp);
     const int nb = (int)(q1 - q0);
     const int nh = tile_nh[src], nmax = tile_nmax[src];
     const int64_t tslots = (int64_t)nh * kWarp;
@@ -394,16 +438,26 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     // groups to the kStreams streams that run one sweep's launches concurrently
     for (LaunchGroup& g : P.groups)
       for (int t = g.tile0; t < g.tile1; ++t) g.work += (int64_t)kWarp * P.tiles[t].nmax * P.tiles[t].nhops;
+    // the long BDDs are one more launch (index -1 here): a warp walks each
+    // level in turn, estimated like a tile level of 16 nodes per level
+    int64_t long_work = 0;
+    for (size_t b = 0; b < long_rows.size(); ++b)
+      long_work += (int64_t)kWarp * 16 * (R->row_ptr[long_rows[b] + 1] - R->row_ptr[long_rows[b]]);
+    auto work_of = [&](int x) { return x < 0 ? long_work : P.groups[x].work; };
     std::vector<int> idx(P.groups.size());
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return P.groups[x].work > P.groups[y].work; });
+    if (!long_rows.empty()) idx.push_back(-1);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return work_of(x) > work_of(y); });
     std::vector<int64_t> load(kStreams, 0);
     for (int gi : idx) {
       int best = 0;
       for (int k = 1; k < kStreams; ++k)
         if (load[k] < load[best]) best = k;
-      P.groups[gi].stream = best;
-      load[best] += P.groups[gi].work;
+      if (gi < 0)
+        P.long_stream = best;
+      else
+        P.groups[gi].stream = best;
+      load[best] += work_of(gi);
     }
   }
   for (const LaunchGroup& g : P.groups) {
@@ -411,6 +465,85 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     for (int t = g.tile0; t < g.tile1; ++t)
       a.region = std::max<int32_t>(a.region, (int32_t)adjoint_smem_bytes(P.tiles[t].nmax, P.tiles[t].nhops));
     P.adj_groups.push_back(a);
+  }
+  // ---- 2b. long BDDs: levels as consecutive slots after the tiles (each
+  // BDD's range padded to a multiple of 32), nodes numbered 2, 3, ... level
+  // by level with 32-bit children (0 top, 1 bottom), and per node its
+  // in-arcs in (parent, beta) order
+  P.long_slot_base = (int32_t)slot_base;
+  {
+    int64_t lslot = slot_base, code_base = 0, lvl_base = 0, cost_base = 0, wpos = 0, rpos = 0;
+    P.longs.resize(long_rows.size());
+    P.long_rank_ptr.assign(long_rows.size() + 1, 0);
+    P.long_code.resize(num_long_nodes);
+    P.long_in_ptr.assign(num_long_nodes + 1, 0);
+    std::vector<int32_t> first;
+    for (size_t b = 0; b < long_rows.size(); ++b) {
+      const int64_t j = long_rows[b];
+      const int k = (int)(R->row_ptr[j + 1] - R->row_ptr[j]);
+      LongBdd& L = P.longs[b];
+      L.slot_base = (int32_t)lslot;
+      L.k = k;
+      L.code_base = (int32_t)code_base;
+      L.lvl_base = (int32_t)lvl_base;
+      L.cost_base = (int32_t)cost_base;
+      L.row = (int32_t)j;
+      L.maxw = 0;
+      first.assign(k + 1, 2);
+      for (int h = 0; h < k; ++h) {
+        const int w = long_width[wpos + h];
+        first[h + 1] = first[h] + w;
+        L.maxw = std::max(L.maxw, w);
+      }
+      L.nn = first[k] - 2;
+      P.long_lvl.insert(P.long_lvl.end(), first.begin(), first.end());
+      const int64_t tslots = ((int64_t)k + kWarp - 1) / kWarp * kWarp;
+      P.desc.resize(lslot + tslots, 0);
+      P.slot_var.resize(lslot + tslots, -1);
+      P.slot_row.resize(lslot + tslots, -1);
+      P.slot_to_csr.resize(lslot + tslots, -1);
+      for (int h = 0; h < k; ++h) {
+        const int64_t csr = R->row_ptr[j] + h, sl = lslot + h;
+        P.slot_var[sl] = R->col[csr];
+        P.slot_row[sl] = (int32_t)j;
+        P.slot_to_csr[sl] = csr;
+        slot_of_csr[csr] = sl;
+      }
+      // children as node numbers; in-degree counts
+      P.long_rank_ptr[b] = rpos;
+      for (int h = 0; h < k; ++h)
+        for (int r = 0; r < long_width[wpos + h]; ++r) {
+          auto num = [&](int32_t rank) -> int32_t {
+            return rank == kCodeBot ? (int32_t)kBotCode : (rank == kCodeTop ? (int32_t)kTopCode : first[h + 1] + rank);
+          };
+          const int32_t lo = num(P.long_lo[rpos]), hi = num(P.long_hi[rpos]);
+          int2& cc = P.long_code[code_base + (first[h] - 2) + r];
+          cc.x = lo;
+          cc.y = hi;
+          if (lo >= 2) P.long_in_ptr[code_base + (lo - 2) + 1]++;
+          if (hi >= 2) P.long_in_ptr[code_base + (hi - 2) + 1]++;
+          ++rpos;
+        }
+      wpos += k;
+      lslot += tslots;
+      code_base += L.nn;
+      lvl_base += k + 1;
+      cost_base += L.nn + 2;
+    }
+    P.long_rank_ptr[long_rows.size()] = rpos;
+    for (int64_t g = 0; g < num_long_nodes; ++g) P.long_in_ptr[g + 1] += P.long_in_ptr[g];
+    P.long_in.assign(P.long_in_ptr[num_long_nodes], 0);
+    std::vector<int32_t> fill(P.long_in_ptr.begin(), P.long_in_ptr.end() - 1);
+    for (const LongBdd& L : P.longs)  // parents ascending, the 0-arc first
+      for (int n = 2; n < L.nn + 2; ++n) {
+        const int2 c = P.long_code[L.code_base + n - 2];
+        if (c.x >= 2) P.long_in[fill[L.code_base + c.x - 2]++] = n << 1;
+        if (c.y >= 2) P.long_in[fill[L.code_base + c.y - 2]++] = (n << 1) | 1;
+      }
+    slot_base = lslot;
+    if (cost_base >= (int64_t)INT32_MAX || P.long_in_ptr[num_long_nodes] >= (int64_t)INT32_MAX)
+      return fail(DG_EINVAL, "dg_plan: long BDDs exceed 2^31 nodes or arcs");
+    P.long_cost_size = (int32_t)cost_base;
   }
   const int64_t num_slots = slot_base;
   if (num_slots >= (int64_t)INT32_MAX || node_base >= (int64_t)INT32_MAX)
@@ -481,10 +614,17 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.lb_chunks = put((size_t)num_chunks * 16);
   P.off.inst_chunk_ptr = put((size_t)(ni + 1) * 4);
   P.off.inst_unc = put((size_t)ni * 8);
+  P.off.longs = put(P.longs.size() * sizeof(LongBdd));
+  P.off.long_code = put(P.long_code.size() * sizeof(int2));
+  P.off.long_lvl = put(P.long_lvl.size() * 4);
+  P.off.long_in_ptr = put(P.long_in_ptr.size() * 4);
+  P.off.long_in = put(P.long_in.size() * 4);
   P.off.S = put((size_t)n * 4);
   P.off.Sbar = put((size_t)n * 4);
   P.off.E = put((size_t)m * 4);
   P.off.lb_part = put((size_t)num_chunks * 8);
+  P.off.long_d = put((size_t)P.long_cost_size * 4);
+  P.off.long_t = put((size_t)P.long_cost_size * 4);
   P.off.total = o;
   P.smem_sweep = align_up(smem_max, 16);
   P.smem_adjoint = align_up(smem_adj_max, 16);
@@ -503,6 +643,8 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   z.max_width = max_width;
   z.smem_bytes = P.smem_sweep;
   z.num_launch_groups = (int32_t)P.groups.size();
+  z.num_long_bdds = (int64_t)P.longs.size();
+  z.num_long_nodes = num_long_nodes;
   return DG_OK;
 }
 
@@ -581,7 +723,70 @@ dg_status validate_plan(const Plan& P) {
     node_base += (int64_t)(tl.nmax - 2) * kWarp;
     slot_base += (int64_t)tl.nhops * kWarp;
   }
-  if (node_base != P.sizes.num_nodes_padded || slot_base != NS) return bad("tiles do not cover the arrays");
+  if (node_base != P.sizes.num_nodes_padded || slot_base != P.long_slot_base) return bad("tiles do not cover the arrays");
+  // long BDDs: consecutive slot ranges after the tiles, levels and children
+  // consistent, in-arc lists exactly the arcs into each node in (parent,
+  // beta) order
+  {
+    int64_t lslot = P.long_slot_base, code_base = 0, lvl_base = 0, cost_base = 0;
+    for (size_t b = 0; b < P.longs.size(); ++b) {
+      const LongBdd& L = P.longs[b];
+      const std::string at = "long BDD " + std::to_string(b) + ": ";
+      if (L.slot_base != lslot || L.code_base != code_base || L.lvl_base != lvl_base || L.cost_base != cost_base ||
+          L.k < 1 || L.nn < 1 || L.row < 0 || L.row >= m || P.long_of_row[L.row] != (int32_t)b)
+        return bad(at + "bases or shape inconsistent");
+      const int32_t* lvl = P.long_lvl.data() + L.lvl_base;
+      if ((size_t)(L.lvl_base + L.k + 1) > P.long_lvl.size() || lvl[0] != 2 || lvl[1] != 3 || lvl[L.k] != L.nn + 2)
+        return bad(at + "level table inconsistent");
+      const int64_t tslots = ((int64_t)L.k + kWarp - 1) / kWarp * kWarp;
+      int row = -1;
+      for (int64_t q = lslot; q < lslot + tslots; ++q) {
+        const int h = (int)(q - lslot);
+        if (h >= L.k) {
+          if (P.slot_var[q] != -1 || P.slot_to_csr[q] != -1) return bad(at + "padding slot in use");
+          continue;
+        }
+        if (lvl[h + 1] <= lvl[h]) return bad(at + "empty level");
+        if (P.slot_var[q] < 0 || P.slot_var[q] >= n) return bad(at + "variable id out of range");
+        if (row < 0) row = P.slot_row[q];
+        if (P.slot_row[q] != row || row != L.row) return bad(at + "slot rows differ");
+        const int64_t c = P.slot_to_csr[q];
+        if (c < 0 || c >= NL || csr_seen[c]++) return bad(at + "slot map not a bijection");
+        real_slots++;
+      }
+      real_nodes += L.nn;
+      std::vector<int32_t> indeg(L.nn + 2, 0);
+      for (int h = 0; h < L.k; ++h)
+        for (int v = lvl[h]; v < lvl[h + 1]; ++v) {
+          const int2 c = P.long_code[L.code_base + v - 2];
+          if (c.x == (int)kBotCode && c.y == (int)kBotCode) return bad(at + "node with no path to top");
+          for (int ch : {c.x, c.y}) {
+            const bool term = ch == (int)kTopCode || ch == (int)kBotCode;
+            const bool in_next = h + 1 < L.k && ch >= lvl[h + 1] && ch < lvl[h + 2];
+            if (h + 1 == L.k ? !term : !(ch == (int)kBotCode || in_next)) return bad(at + "child outside the next level");
+            if (ch >= 2) indeg[ch]++;
+          }
+        }
+      for (int v = 2; v < L.nn + 2; ++v) {
+        const int32_t b0 = P.long_in_ptr[L.code_base + v - 2], b1 = P.long_in_ptr[L.code_base + v - 1];
+        if (b1 - b0 != indeg[v] || (v > 2 && indeg[v] == 0)) return bad(at + "in-arc list size wrong");
+        int32_t prev = -1;
+        for (int32_t i = b0; i < b1; ++i) {
+          const int32_t e = P.long_in[i], par = e >> 1;
+          if (e <= prev || par < 2 || par >= v) return bad(at + "in-arc list not ascending");
+          const int2 c = P.long_code[L.code_base + par - 2];
+          if ((e & 1 ? c.y : c.x) != v) return bad(at + "in-arc is not an arc");
+          prev = e;
+        }
+      }
+      lslot += tslots;
+      code_base += L.nn;
+      lvl_base += L.k + 1;
+      cost_base += L.nn + 2;
+    }
+    if (lslot != NS || cost_base != P.long_cost_size || code_base != P.sizes.num_long_nodes)
+      return bad("long BDDs do not cover the arrays");
+  }
   if (real_slots != NL || real_nodes != P.sizes.num_nodes) return bad("slot or node count mismatch");
   // variables: CSR and ELL columns point back at their own slots, rows ascending
   if ((int64_t)P.var_ptr.size() != (int64_t)n + 1 || P.var_ptr[0] != 0 || P.var_ptr[n] != NL)

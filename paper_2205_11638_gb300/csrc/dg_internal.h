@@ -52,6 +52,25 @@ inline int ring_size(int maxw) {
   return r;
 }
 
+// A BDD beyond the limits of the lane-per-BDD tiles (more than
+// kMaxNodesPerBdd nodes, or a level wider than kMaxWidth): swept by one warp
+// with a level's nodes spread over the lanes.  Its levels are consecutive
+// arena slots; its nodes are numbered like a tile lane's (0 top, 1 bottom,
+// own nodes from 2 level by level) with 32-bit child numbers, and every node
+// lists its in-arcs (parent number << 1 | beta, ascending) for the pulls of
+// SP(r, .).
+struct LongBdd {
+  int32_t slot_base;  // arena slot of level 0
+  int32_t k;          // levels
+  int32_t code_base;  // long_code / long_in_ptr index of node number 2
+  int32_t nn;         // own nodes
+  int32_t lvl_base;   // long_lvl index: k + 1 entries, first node number of each level, then nn + 2
+  int32_t cost_base;  // per-node scratch index of node number 0 (nn + 2 entries)
+  int32_t row;        // original row
+  int32_t maxw;       // widest level
+};
+static_assert(sizeof(LongBdd) == 32, "LongBdd is 32 bytes");
+
 // Device view of an arena (all pointers inside the caller's buffer).
 struct DevArena {
   const Tile* tiles;
@@ -69,6 +88,14 @@ struct DevArena {
   const int4* lb_chunks;    // {instance, kind (0 rows, 1 vars), begin, end}
   const int32_t* inst_chunk_ptr;
   const double* inst_unc;   // per instance: sum of min(0, c_i) over variables no row covers
+  // BDDs swept one warp per BDD (see LongBdd)
+  const LongBdd* longs;
+  const int2* long_code;     // per own node: lo, hi node numbers
+  const int32_t* long_lvl;
+  const int32_t* long_in_ptr;  // CSR of in-arcs over own nodes (global index)
+  const int32_t* long_in;      // parent node number << 1 | beta
+  float* long_d;               // scratch per node of long BDDs: SP(r, .)
+  float* long_t;               // ... SP(., T)
   float* S;                 // scratch: per-variable sum of M (snapshot)
   float* Sbar;              // scratch: S_i / |J_i| (the mode-0 averaging term)
   float* E;                 // scratch: E^j per original row
@@ -79,6 +106,10 @@ struct DevArena {
   int64_t num_slots;
   int32_t num_tiles;
   int32_t num_lb_chunks;
+  int32_t num_long;
+  int32_t long_slot_base;   // first slot of the long BDDs (after every tile's slots)
+  int32_t long_cost_size;   // entries of long_d / long_t
+  int32_t long_stream;      // stream of the fork/join set the long BDDs run on
 };
 
 // Tiles that one kernel launch sweeps: consecutive tiles whose shared-memory
@@ -131,10 +162,20 @@ struct Plan {
   std::vector<int64_t> row_ptr;
   std::vector<int64_t> node_ptr;  // per row, first node
   std::vector<int8_t> lo8, hi8;
+  // long BDDs: per row the index into `longs` (-1 for tile rows), their
+  // device arrays, and for export their levels' widths and child ranks
+  std::vector<int32_t> long_of_row;
+  std::vector<LongBdd> longs;
+  std::vector<int2> long_code;
+  std::vector<int32_t> long_lvl, long_in_ptr, long_in;
+  std::vector<int64_t> long_rank_ptr;  // per long BDD, first entry of long_lo / long_hi
+  std::vector<int32_t> long_lo, long_hi;  // child ranks as in lo8 / hi8 (-2 bottom, -1 top)
+  int32_t long_slot_base = 0, long_cost_size = 0, long_stream = 0;
   // byte offsets of every array inside the arena
   struct Off {
     size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, c, invdeg, inst_row_ptr, inst_var_ptr,
-        lb_chunks, inst_chunk_ptr, inst_unc, S, Sbar, E, lb_part, total;
+        lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, S, Sbar, E, lb_part,
+        long_d, long_t, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels
   size_t smem_adjoint = 0; // dynamic smem of the adjoint kernels

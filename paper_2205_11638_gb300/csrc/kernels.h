@@ -24,6 +24,10 @@ struct SweepArgs {
   uint16_t* rec_meta;  // per node (layout of the child codes): in-arc parent | beta << 8 | hi-choice << 9
   uint16_t* rec_amin;  // per slot: argmin node of m0 | argmin node of m1 << 8
   float* rec_diff;     // per slot: m1 - m0
+  // ... for the long BDDs: per node (cost scratch index) in-arc << 1 |
+  // hi-choice, per long slot (from long_slot_base) the argmin nodes of m0, m1
+  int32_t* rec_lmeta;
+  int2* rec_lamin;
 };
 
 // The caller's stream plus kStreams - 1 auxiliary streams of an arena: the
@@ -77,6 +81,12 @@ struct AdjArgs {
   float* g_omega;          // accumulated
   float* g_alpha;          // accumulated
   float* sdot;             // out: alpha * (gradient of lambda after the sweep), per slot
+  // long BDDs: the records of the sweep and per-node gradient scratch of
+  // SP(., T) and SP(r, .)
+  const int32_t* rec_lmeta;
+  const int2* rec_lamin;
+  float* long_a1;
+  float* long_a2;
 };
 cudaError_t set_adjoint_smem_limit(size_t bytes);
 void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups,
@@ -97,6 +107,12 @@ void launch_param_transform(const DevArena& A, const float* ah, const float* wh,
                             float* omega, float* theta, cudaStream_t st);
 void launch_param_transform_bwd(const DevArena& A, const float* alpha, const float* omega, const float* ga,
                                 const float* gw, const float* gt, float* gah, float* gwh, float* gth, cudaStream_t st);
+
+// Long BDDs, one warp per BDD (kernels_long.cu); each is a single launch on
+// the given stream, or nothing when the arena has no long BDDs.
+void launch_long_sweep(int kind, const DevArena& A, const SweepArgs& a, cudaStream_t st);
+void launch_long_smoothed(const DevArena& A, const float* lam, float a_s, float* E_a, float* marg, cudaStream_t st);
+void launch_long_adjoint(bool forward, const DevArena& A, const AdjArgs& a, cudaStream_t st);
 
 // dg_lower_bound with its intermediates in a static device array (noalloc.cu).
 dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, int num_groups, int threads,

@@ -250,8 +250,9 @@ cudaError_t set_adjoint_smem_limit(size_t bytes) {
 template <int FWD, int MODE>
 static void launch_adj(const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups, size_t cap,
                        const StreamSet& ss) {
-  const bool fork = num_groups > 1 && ss.ready;
+  const bool fork = num_groups + (A.num_long > 0 ? 1 : 0) > 1 && ss.ready;
   if (fork) ss.begin();
+  launch_long_adjoint(FWD != 0, A, a, fork ? ss.of(A.long_stream) : ss.main);
   for (int g = 0; g < num_groups; ++g) {
     const AdjGroup& G = groups[g];
     const size_t region = (size_t)G.region;

@@ -243,10 +243,10 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
     for (int o = lane; o < (s.nmax - 2) * (kWarp / 2); o += kWarp) dst[o] = src[o];
   }
 
-  if ((KIND == kBwd || KIND == kEnergy) && a.E != nullptr && lane < T.nbdd) {
+  if ((BWD || KIND == kEnergy) && a.E != nullptr && lane < T.nbdd) {
     // SP(root, T) = E^j of my BDD
     const int row = __ldg(A.slot_row + sbase + lane);
-    a.E[row] = KIND == kBwd ? DG_W(s, 2) : DG_F(s, 2);
+    a.E[row] = BWD ? DG_W(s, 2) : DG_F(s, 2);
   }
 }
 
@@ -319,8 +319,9 @@ __global__ void __launch_bounds__(128) k_smoothed(DevArena A, const float* lam, 
 
 void launch_smoothed(const DevArena& A, const float* lam, float a_s, float* E_a, float* marg, const LaunchGroup* groups,
                      int num_groups, const StreamSet& ss) {
-  const bool fork = num_groups > 1 && ss.ready;
+  const bool fork = num_groups + (A.num_long > 0 ? 1 : 0) > 1 && ss.ready;
   if (fork) ss.begin();
+  launch_long_smoothed(A, lam, a_s, E_a, marg, fork ? ss.of(A.long_stream) : ss.main);
   for (int g = 0; g < num_groups; ++g) {
     const LaunchGroup& G = groups[g];
     const size_t region = (size_t)G.region_bwd0;
@@ -392,8 +393,10 @@ void StreamSet::end() const {
 template <int KIND, int MODE>
 static void launch_groups(const DevArena& A, const SweepArgs& a, int threads, const LaunchGroup* groups,
                           int num_groups, const StreamSet& ss) {
-  const bool fork = num_groups > 1 && ss.ready;
+  const bool fork = num_groups + (A.num_long > 0 ? 1 : 0) > 1 && ss.ready;
   if (fork) ss.begin();
+  // the long BDDs first: their launch is a few warps walking long chains
+  launch_long_sweep(KIND, A, a, fork ? ss.of(A.long_stream) : ss.main);
   for (int g = 0; g < num_groups; ++g) {
     const LaunchGroup& G = groups[g];
     constexpr bool REC = KIND == kFwdRec || KIND == kBwdRec;

@@ -6,14 +6,16 @@
 // whose allocator is owned by another runtime, or a serving loop with a
 // fixed, pre-planned memory budget.  dg_lower_bound writes its intermediates
 // (E^j per row, S_i and S_i / |J_i| per variable, one FP64 partial sum per
-// reduction chunk) into the scratch area of the caller's arena buffer; this
+// reduction chunk, the path costs of long BDDs) into the scratch area of the
+// caller's arena buffer; this
 // variant keeps them in one file-scope __device__ array instead, so the
 // caller passes only the inputs (lambda, M) and the output (bound per
 // instance).  The arena's own scratch area is left untouched.
 //
 // Limits and sharing:
 //  * the array holds kNoallocScratchBytes (4 MiB); arenas whose intermediates
-//    need more (4 m + 8 n + 8 chunks bytes) are rejected with DG_EINVAL;
+//    need more (4 m + 8 n + 8 chunks + 4 per node of the long BDDs bytes) are
+//    rejected with DG_EINVAL;
 //  * every GPU that loads libdg holds the array until the process exits;
 //  * all calls share it: two calls whose kernels overlap on the GPU (on
 //    different streams, or from different host threads) race on it.  Calls
@@ -69,11 +71,12 @@ dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, 
   cudaStream_t st = ss.main;
   const size_t bE = up256((size_t)arena.m * 4), bS = up256((size_t)arena.n * 4);
   const size_t bP = up256((size_t)arena.num_lb_chunks * 8);
-  const size_t need = bE + 2 * bS + bP;
+  const size_t bL = up256((size_t)arena.long_cost_size * 4);
+  const size_t need = bE + 2 * bS + bP + bL;
   if (need > kNoallocScratchBytes)
     return fail(DG_EINVAL, "dg_lower_bound_noalloc: this arena needs " + std::to_string(need) +
                                " bytes of scratch, more than the " + std::to_string(kNoallocScratchBytes) +
-                               " bytes of the static array (4 m + 8 n + 8 chunks must fit)");
+                               " bytes of the static array (4 m + 8 n + 8 chunks + 4 per long-BDD node must fit)");
   void* base = nullptr;
   if (dg_status s = noalloc_scratch(&base)) return s;
   char* p = static_cast<char*>(base);
@@ -82,6 +85,8 @@ dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, 
   A.S = reinterpret_cast<float*>(p + bE);
   A.Sbar = reinterpret_cast<float*>(p + bE + bS);
   A.lb_part = reinterpret_cast<double*>(p + bE + 2 * bS);
+  A.long_t = reinterpret_cast<float*>(p + bE + 2 * bS + bP);  // SP(., T) of the long BDDs' nodes
+  A.long_d = nullptr;                                         // not read by the energy pass
   SweepArgs a{};
   a.lam = const_cast<float*>(lam);
   a.E = A.E;

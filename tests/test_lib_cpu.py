@@ -86,6 +86,27 @@ def test_plan_random_rows_bit_exact():
             np.testing.assert_array_equal(a, b)
 
 
+def test_plan_wide_coefficient_rows_bit_exact():
+    """Rows with coefficients in [-12, 12] (the builder clamps partial sums to
+    the window where residual functions still differ) keep the oracle's BDDs,
+    bit for bit, for every sense."""
+    rows = []
+    for r in workloads.random_rows(700, kmax=14, n=40, amax=12, seed=91):
+        try:
+            oracle.Oracle(workloads.single_rows_problem([r], 40, np.zeros(40)))
+        except oracle.OracleError:
+            continue
+        rows.append(r)
+    assert len({r[2] for r in rows}) == 3
+    prob = workloads.single_rows_problem(rows, 40, np.zeros(40))
+    P = solver.plan(prob)
+    O = oracle.Oracle(prob)
+    for j in range(P.m):
+        for a, b in zip(P.bdd(j), O.bdd(j)):
+            np.testing.assert_array_equal(a, b)
+    P.validate()
+
+
 def test_slot_map_is_permutation():
     prob = workloads.matching_quadratic(L=30, R=30, pairs=900, seed=5)
     P = solver.plan(prob, tile_nodes=256, tile_slots=128)
@@ -107,9 +128,8 @@ def _status_of(rows, n):
 def test_status_codes():
     assert _status_of([(np.array([0, 1]), np.array([2, 2]), 2, 1)], 2) == _lib.DG_EINFEASIBLE
     assert _status_of([(np.array([0, 1]), np.array([1, 1]), 1, 2)], 2) == _lib.DG_EFORCED
-    # a knapsack row whose BDD has more than 254 nodes (a level of 112)
-    a = np.array([28, 31, 45, 57, 3, 9, 49, 56, 15, 19, 52, 25, 17, 49, 16, 25])
-    assert _status_of([(np.arange(16), a, 0, 248)], 16) == _lib.DG_EINVAL
+    # more than 4096 variables in a row
+    assert _status_of([(np.arange(4097), np.ones(4097, np.int64), 0, 1)], 4097) == _lib.DG_EINVAL
     bad = workloads.single_rows_problem([(np.array([0, 1]), np.array([1, 1]), 0, 1)], 2, np.zeros(2))
     bad["col"] = bad["col"][::-1].copy()
     with pytest.raises(_lib.DgError) as e:
@@ -122,18 +142,46 @@ def test_status_codes():
     assert e.value.status == _lib.DG_EINVAL
 
 
-def test_bdd_node_limit():
-    """A BDD of exactly 254 nodes (x_0 + ... + x_29 <= 14) is accepted; one
-    more variable and a larger bound exceed the 8-bit node numbers and the
-    row is rejected with DG_EINVAL and a message naming it."""
-    ok = workloads.single_rows_problem([(np.arange(30), np.ones(30, np.int64), 0, 14)], 30, np.zeros(30))
-    P = solver.plan(ok)
-    assert len(P.bdd(0)[1]) == 254
+def _bit_exact(prob):
+    P = solver.plan(prob)
+    O = oracle.Oracle(prob)
+    assert P.sizes.num_nodes == O.num_nodes
+    for j in range(P.m):
+        for a, b in zip(P.bdd(j), O.bdd(j)):
+            np.testing.assert_array_equal(a, b)
     P.validate()
+    return P
+
+
+def test_bdd_size_limits_route_rows_to_the_long_layout():
+    """A BDD of exactly 254 nodes (x_0 + ... + x_29 <= 14) fits a tile lane;
+    one more node, or a level of more than 128 nodes, makes the row a long
+    BDD (one warp per BDD) instead of an error.  Either way the structure is
+    the oracle's, bit for bit, and the arena passes the validator."""
+    ok = workloads.single_rows_problem([(np.arange(30), np.ones(30, np.int64), 0, 14)], 30, np.zeros(30))
+    P = _bit_exact(ok)
+    assert len(P.bdd(0)[1]) == 254 and P.sizes.num_long_bdds == 0
     big = workloads.single_rows_problem([(np.arange(60), np.ones(60, np.int64), 0, 30)], 60, np.zeros(60))
-    with pytest.raises(_lib.DgError, match="more than 254 nodes") as e:
-        solver.plan(big)
-    assert e.value.status == _lib.DG_EINVAL
+    P = _bit_exact(big)
+    assert P.sizes.num_long_bdds == 1 and P.sizes.num_long_nodes == P.sizes.num_nodes > 254
+    assert P.sizes.num_tiles == 0
+    # a knapsack row with a level of 112 nodes and more than 254 in all
+    a = np.array([28, 31, 45, 57, 3, 9, 49, 56, 15, 19, 52, 25, 17, 49, 16, 25])
+    P = _bit_exact(workloads.single_rows_problem([(np.arange(16), a, 0, 248)], 16, np.zeros(16)))
+    assert P.sizes.num_long_bdds == 1
+
+
+def test_long_and_tile_rows_mixed_in_one_arena():
+    """Cardinality rows over 500 variables, a knapsack row with a level wider
+    than 128 nodes and ordinary short rows in one arena: every row keeps the
+    oracle's BDD; the long BDDs' slots follow the tiles' and the slot map is
+    a permutation of the CSR positions."""
+    prob = workloads.long_rows_mix(seed=3)
+    P = _bit_exact(prob)
+    assert P.sizes.num_long_bdds >= 3 and P.sizes.max_width > 128
+    sm = P.slot_to_csr
+    real = sm[sm >= 0]
+    assert sorted(real.tolist()) == list(range(len(prob["col"])))
 
 
 def test_problem_without_rows_plans_empty_arena():

@@ -16,10 +16,12 @@ from paper_2205_11638_gb300 import _lib, build, solver
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_bound_matches_lower_bound_twice():
+@pytest.mark.parametrize("make", [lambda: workloads.matching_quadratic(L=80, R=80, pairs=4000, seed=11),
+                                  lambda: workloads.long_rows_mix(seed=5)], ids=["tiles", "with_long_bdds"])
+def test_noalloc_bound_matches_lower_bound_twice(make):
     build.build()
     lib = _lib.load()
-    prob = workloads.matching_quadratic(L=80, R=80, pairs=4000, seed=11)
+    prob = make()
     A = solver.plan(prob).bind()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     lam, M = A.init_lambda()

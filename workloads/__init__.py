@@ -291,6 +291,65 @@ def random_rows(num, kmax=14, n=None, amax=3, seed=0, allow_eq=True):
     return rows
 
 
+def _free_row(row):
+    """True if every variable of a short row takes both values in some
+    feasible assignment (enumeration of its 2^k assignments)."""
+    _, a, sense, b = row
+    a = np.asarray(a, np.int64)
+    k = len(a)
+    x = (np.arange(1 << k)[:, None] >> np.arange(k)[None, :]) & 1
+    act = x @ a
+    ok = act <= b if sense == LE else (act >= b if sense == GE else act == b)
+    if not ok.any():
+        return False
+    feas = x[ok]
+    return bool(np.all(feas.min(axis=0) == 0) and np.all(feas.max(axis=0) == 1))
+
+
+def long_rows_mix(seed=BASE_SEED + 6, n_short=40):
+    """Rows whose BDDs are too large for a tile lane, mixed with short ones:
+    cardinality rows over 500 variables (sum <= 1, sum <= 10, sum = 25),
+    sum >= 1 over 300 variables, a knapsack row sum_i i * x_i <= 200 over 30
+    variables (a level of more than 128 nodes), and random short rows over
+    the first 40 variables.  Costs N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    n = 700
+    rows = [(np.sort(rng.choice(n, size=500, replace=False)), np.ones(500, np.int64), LE, 1),
+            (np.sort(rng.choice(n, size=500, replace=False)), np.ones(500, np.int64), LE, 10),
+            (np.sort(rng.choice(n, size=500, replace=False)), np.ones(500, np.int64), EQ, 25),
+            (np.sort(rng.choice(n, size=300, replace=False)), np.ones(300, np.int64), GE, 1),
+            (np.arange(600, 630), np.arange(1, 31), LE, 200)]
+    short = []
+    for r in random_rows(8 * n_short, kmax=6, n=40, seed=seed + 1):
+        if _free_row(r):
+            short.append(r)
+        if len(short) == n_short:
+            break
+    return single_rows_problem(rows + short, n, rng.normal(size=n))
+
+
+def assignment(L=2000, R=2000, cand=300, seed=BASE_SEED + 7):
+    """Sparse assignment (graph-matching-like) instance with long rows: every
+    left node has ``cand`` distinct random right candidates (variable x_lr,
+    cost N(0, 1)); rows sum_r x_lr <= 1 per left node and sum_l x_lr <= 1 per
+    right node (about ``cand`` variables each)."""
+    rng = np.random.default_rng(seed)
+    rights = np.stack([np.sort(rng.choice(R, size=cand, replace=False)) for _ in range(L)])
+    n = L * cand
+    var = np.arange(n, dtype=np.int64)
+    left = np.repeat(np.arange(L), cand)
+    right = rights.reshape(-1)
+    row_of = np.concatenate([left, L + right])
+    vv = np.concatenate([var, var])
+    m = L + R
+    sense = np.full(m, LE, np.int8)
+    rhs = np.ones(m, np.int32)
+    keep = np.bincount(row_of, minlength=m) > 0
+    remap = np.cumsum(keep) - 1
+    return _csr_from_flat(n, remap[row_of], vv, np.ones(len(vv), np.int64), sense[keep], rhs[keep],
+                          rng.normal(size=n))
+
+
 def single_rows_problem(rows, n, c):
     """One problem from a list of (vars, coefs, sense, rhs) rows."""
     return _pack(n, [r[0] for r in rows], [r[1] for r in rows], [r[2] for r in rows],
@@ -303,4 +362,5 @@ CONFIGS = {
     "matching_quadratic_200": lambda: matching_quadratic(),
     "batched_mix_64": lambda: batched_mix()[0],
     "tracking_500x2000": lambda: tracking(),
+    "assignment_2000x300": lambda: assignment(),
 }
