@@ -42,6 +42,7 @@ WORKLOADS = {
     "tracking_200x2000": lambda: workloads.tracking(frames=200),
     "matching_quadratic_200": lambda: workloads.matching_quadratic(),
     "independent_set_10k": lambda: workloads.independent_set(),
+    "assignment_2000x300": lambda: workloads.assignment(),
 }
 
 
@@ -480,8 +481,19 @@ def _oracle_leg(args, A, prob, solver, torch, keep):
     olb1 = O.lower_bound(ol, oM)
     el = float(np.abs(A.to_csr(lam).double().cpu().numpy() - ol).max())
     eM = float(np.abs(A.to_csr(M).double().cpu().numpy() - oM).max())
+    # the FP64 summation of the bound: the GPU's bound against the exactly
+    # rounded sum (math.fsum) of its own float32 terms E^j and min(0, S_i)
+    import math
+    lbE, E = A.lower_bound(lam, M, energies=True)
+    Sf = np.zeros(prob["n"], np.float32)
+    np.add.at(Sf, prob["col"], A.to_csr(M).cpu().numpy().astype(np.float32))
+    covered = np.bincount(prob["col"], minlength=prob["n"]) > 0
+    exact = math.fsum(E.cpu().numpy().astype(np.float64).tolist() +
+                      np.minimum(0.0, Sf.astype(np.float64)).tolist() +
+                      np.minimum(0.0, prob["c"][~covered]).tolist())
     par[args.workload] = {"lambda_max_abs_err_over_max_c": el / cmax, "M_max_abs_err_over_max_c": eM / cmax,
                           "bound_after_1_iteration": lb1, "bound_rel_err": abs(lb1 - olb1) / max(1.0, abs(olb1)),
+                          "bound_fp64_sum_rel_err_vs_exact_sum_of_its_terms": abs(float(lbE[0]) - exact) / abs(exact),
                           "iterations": 1, "oracle_s": time.perf_counter() - t0}
     del O, ol, oM
     # (b) 50-frame slice of the same generator: bound after 100 iterations;
@@ -682,6 +694,7 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": sweep_ms,
             "iteration_algorithmic_bytes": st.bytes_per_iter,
             "iteration_frac": st.bytes_per_iter / (ms_per_step * 1e-3) / 1e9 / peak,
+            "dram_traffic_frac": (traffic / (sweep_ms * 1e-3) / 1e9 / peak) if traffic else None,
             "kernel_source_sha": src_sha}
     shares = {"k_sweep_fwd": sum(t_fwd), "k_reduce_S": sum(t_red) + 0.0, "k_sweep_bwd": sum(t_bwd),
               "k_reduce_S+k_lb": sum(t_tail)}
@@ -769,7 +782,7 @@ def run_ours(args):
     if not args.no_batched:
         batched, keep["batched"] = _batched_measurement(args, solver, torch)
     matching_adjoint = None
-    if not args.no_adjoint:
+    if not args.no_adjoint and not args.no_matching:
         matching_adjoint, keep["matching"] = _matching_adjoint_measurement(solver, torch)
     independent_set = None
     if not args.no_is:
@@ -826,6 +839,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-is", action="store_true")
     ap.add_argument("--no-long", action="store_true")
+    ap.add_argument("--no-matching", action="store_true")
     ap.add_argument("--adjoint-iters", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
