@@ -208,9 +208,13 @@ dg_status dg_iterate(dg_arena* arena, void* stream, float* lam, float* M, const 
 /* The building blocks dg_iterate chains, for custom schedules and per-kernel
  * timing.  dg_sum_M stores the snapshot S_i = sum_{j in J_i} M_ij inside the
  * arena (with renorm != 0 it also re-projects lam onto
- * sum_j (lambda_ij + M_ij) = c_i in FP64, weights as in mode).  dg_sweep runs
- * one sweep of Alg. 1 (forward != 0: blocks B_1..B_u, else B_u..B_1) with
- * that snapshot; with want_energy (backward sweeps only) it also stores
+ * sum_j (lambda_ij + M_ij) = c_i in FP64, weights as in mode) and gives every
+ * slot (i,j) the averaging term of mode (S_i / |J_i| in mode 0, S_i in mode
+ * 1, which the sweep weights by alpha_ij).  dg_sweep runs one sweep of
+ * Alg. 1 (forward != 0: blocks B_1..B_u, else B_u..B_1) with that snapshot,
+ * in the mode of the arena's last dg_sum_M (or S reduction of another call
+ * that sweeps: dg_iterate, the checkpointed calls, dg_autotune in mode 0),
+ * else DG_EINVAL; with want_energy (backward sweeps only) it also stores
  * E^j(lambda) of every row in the arena.  dg_bound_from_energies writes the
  * per-instance lower bound from the stored E and S (float64[num_inst]).
  * dg_iterate(iters) = dg_sum_M, then per iteration: dg_sweep(forward),

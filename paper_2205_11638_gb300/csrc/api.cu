@@ -38,6 +38,9 @@ struct dg_arena_s {
   size_t smem_sweep = 0, smem_adjoint = 0;
   int device = 0;
   int max_tile_rows = 0, max_tile_slots = 0, max_tile_hops = 0;
+  // mode of the averaging terms the last S reduction for a sweep wrote into
+  // the per-slot array (-1: none yet, the array holds zeros)
+  int avg_mode = -1;
 };
 
 struct dg_graph_s {
@@ -81,15 +84,16 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   a.alpha = alpha;
   a.omega0 = omega_of(opts);
   a.mode = mode;
-  launch_reduce_S(A, M, lam, alpha, mode, false, st);
+  ar->avg_mode = mode;
+  launch_reduce_S(A, M, lam, alpha, mode, false, st, true);
   for (int it = 0; it < iters; ++it) {
     a.E = nullptr;
     launch_sweep(kFwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
-    launch_reduce_S(A, M, lam, alpha, mode, false, st);
+    launch_reduce_S(A, M, lam, alpha, mode, false, st, true);
     if (lb_out && it == iters - 1) a.E = A.E;
     launch_sweep(kBwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
-    launch_reduce_S(A, M, lam, alpha, mode, rn, st);
+    launch_reduce_S(A, M, lam, alpha, mode, rn, st, it + 1 < iters);
   }
   if (lb_out) {
     if (iters == 0) {
@@ -338,6 +342,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.long_t = (float*)(b + P.off.long_t);
   A.S = (float*)(b + P.off.S);
   A.Sbar = (float*)(b + P.off.Sbar);
+  A.slot_avg = (float*)(b + P.off.slot_avg);
   A.E = (float*)(b + P.off.E);
   A.lb_part = (double*)(b + P.off.lb_part);
   A.n = P.sizes.n;
@@ -439,7 +444,8 @@ dg_status dg_autotune(dg_arena* ar, void* stream, float* lam, float* M, int32_t 
     cudaEventElapsedTime(&ms, e0, e1);
     return ms / reps;
   };
-  launch_reduce_S(A, M, nullptr, nullptr, 0, false, st);
+  ar->avg_mode = 0;
+  launch_reduce_S(A, M, nullptr, nullptr, 0, false, st, true);
   auto pair = [&] {
     launch_sweep(kFwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     launch_sweep(kBwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
@@ -509,7 +515,8 @@ dg_status dg_sum_M(dg_arena* ar, void* stream, const float* M, float* lam, const
   if (dg_status s = check_state(ar)) return s;
   if (!M || (renorm && !lam)) return fail(DG_EINVAL, "dg_sum_M: null pointer");
   if (renorm && mode == 1 && !alpha) return fail(DG_EINVAL, "dg_sum_M: mode 1 needs alpha");
-  launch_reduce_S(ar->dev, M, lam, alpha, mode, renorm != 0, (cudaStream_t)stream);
+  ar->avg_mode = mode;
+  launch_reduce_S(ar->dev, M, lam, alpha, mode, renorm != 0, (cudaStream_t)stream, true);
   return check_launch("dg_sum_M");
 }
 
@@ -520,6 +527,8 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_sweep: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_sweep: mode 1 needs omega and alpha");
   if (forward && want_energy) return fail(DG_EINVAL, "dg_sweep: energies come from backward sweeps");
+  if (ar->avg_mode >= 0 && ar->avg_mode != mode)
+    return fail(DG_EINVAL, "dg_sweep: mode differs from the one the arena's last S reduction (dg_sum_M) was run in");
   if (dg_status s = check_vectors("dg_sweep", lam, M, omega, alpha)) return s;
   SweepArgs a{};
   a.lam = lam;
@@ -564,7 +573,7 @@ dg_status dg_lower_bound(dg_arena* ar, void* stream, const float* lam, const flo
   a.E = ar->dev.E;
   launch_sweep(kEnergy, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(),
                streams_for(ar, st));
-  launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
+  launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st, false);
   launch_lower_bound(ar->dev, lb, st);
   if (E_per_row) {
     cudaError_t e = cudaMemcpyAsync(E_per_row, ar->dev.E, (size_t)ar->dev.m * 4, cudaMemcpyDeviceToDevice, st);
@@ -592,7 +601,7 @@ dg_status dg_lb_seed(dg_arena* ar, void* stream, const float* lam, const float* 
   a.M = g_lam;
   launch_sweep(kSeed, ar->dev, a, threads_of(nullptr), ar->groups.data(), (int)ar->groups.size(),
                streams_for(ar, st));
-  launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st);
+  launch_reduce_S(ar->dev, M, nullptr, nullptr, 0, false, st, false);
   launch_seed_M(ar->dev, g_M, st);
   return check_launch("dg_lb_seed");
 }
@@ -755,8 +764,9 @@ dg_status enqueue_recorded_segment(dg_arena* ar, cudaStream_t st, float* lam, fl
   fa.omega0 = omega_of(opts);
   fa.mode = mode;
   cudaError_t e = cudaSuccess;
+  ar->avg_mode = mode;
   for (int sw = 0; sw < 2 * k; ++sw) {
-    launch_reduce_S(A, M, nullptr, nullptr, mode, false, st);
+    launch_reduce_S(A, M, nullptr, nullptr, mode, false, st, true);
     if (e == cudaSuccess && n)
       e = cudaMemcpyAsync(w + L.seg_S + (size_t)sw * n * 4, A.S, n * 4, cudaMemcpyDeviceToDevice, st);
     SweepArgs ra = fa;
@@ -769,7 +779,7 @@ dg_status enqueue_recorded_segment(dg_arena* ar, cudaStream_t st, float* lam, fl
     launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads_of(opts), ar->groups.data(), (int)ar->groups.size(),
                  streams_for(ar, st));
   }
-  launch_reduce_S(A, M, nullptr, nullptr, mode, false, st);
+  launch_reduce_S(A, M, nullptr, nullptr, mode, false, st, false);
   if (lb_out) launch_lower_bound(A, lb_out, st);
   if (e != cudaSuccess) return cuda_fail(e, "recorded segment copies");
   return check_launch("recorded segment");
@@ -813,6 +823,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
     return fail(DG_EINVAL, "dg_backward: workspace smaller than dg_backward_workspace_bytes()");
   cudaStream_t st = (cudaStream_t)stream;
   const DevArena& A = ar->dev;
+  if (iters > 0) ar->avg_mode = mode;
   const size_t NS = (size_t)ar->sizes.num_slots, n = (size_t)ar->sizes.n;
   const size_t bNS = NS * 4, bn = n * 4;
   cudaError_t e = cudaSuccess;
@@ -865,9 +876,9 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       break;
     }
     for (int it = 0; it < L.k; ++it) {
-      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
+      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);
       launch_sweep(kFwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
-      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
+      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);
       launch_sweep(kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     }
   }
@@ -897,7 +908,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       cpy(w_M, ck_M + (size_t)c * NS, bNS);
     }
     for (int sw = 0; sw < (recorded ? 0 : nsw); ++sw) {
-      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st);
+      launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);
       cpy(seg_S + (size_t)sw * n, A.S, bn);
       SweepArgs ra = fa;
       ra.rec_meta = (uint16_t*)(rec_meta + (size_t)sw * L.meta_stride);

@@ -621,6 +621,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.long_in = put(P.long_in.size() * 4);
   P.off.S = put((size_t)n * 4);
   P.off.Sbar = put((size_t)n * 4);
+  P.off.slot_avg = put((size_t)num_slots * 4);
   P.off.E = put((size_t)m * 4);
   P.off.lb_part = put((size_t)num_chunks * 8);
   P.off.long_d = put((size_t)P.long_cost_size * 4);

@@ -98,6 +98,8 @@ struct DevArena {
   float* long_t;               // ... SP(., T)
   float* S;                 // scratch: per-variable sum of M (snapshot)
   float* Sbar;              // scratch: S_i / |J_i| (the mode-0 averaging term)
+  float* slot_avg;          // scratch per slot: the averaging term of its variable (Sbar_i in mode 0,
+                            // S_i in mode 1) as the last S reduction before a sweep left it; 0 for padding
   float* E;                 // scratch: E^j per original row
   double* lb_part;          // scratch: one partial sum per lb chunk
   int32_t n;
@@ -174,7 +176,7 @@ struct Plan {
   // byte offsets of every array inside the arena
   struct Off {
     size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, c, invdeg, inst_row_ptr, inst_var_ptr,
-        lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, S, Sbar, E, lb_part,
+        lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, S, Sbar, slot_avg, E, lb_part,
         long_d, long_t, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels

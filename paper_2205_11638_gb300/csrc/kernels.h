@@ -58,8 +58,10 @@ void launch_sweep(int kind, const DevArena& A, const SweepArgs& a, int threads, 
 
 // S_i = sum_{k in J_i} M_ik in fixed slot order; with renorm, also
 // lambda_ij += alpha_ij * (c_i - sum_k (lambda_ik + M_ik)) computed in FP64.
+// With for_sweep, also the mode's averaging term of every slot into
+// A.slot_avg, where the next sweeps read it.
 void launch_reduce_S(const DevArena& A, const float* M, float* lam, const float* alpha, int mode, bool renorm,
-                     cudaStream_t st);
+                     cudaStream_t st, bool for_sweep);
 void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st);
 // per-instance FP64 lower bound from A.E and A.S
 void launch_lower_bound(const DevArena& A, double* lb_out, cudaStream_t st);

@@ -11,7 +11,11 @@ namespace dg {
 // renorm the same pass re-projects lambda onto sum_j (lambda_ij + M_ij) = c_i
 // (the invariant of the proof of Prop. 1): the FP64 residual
 // r_i = c_i - sum_j (lambda_ij + M_ij) is spread with the averaging weights.
-template <bool RENORM>
+// With SCATTER every slot of the variable also receives the averaging term
+// the sweeps add (Sbar_i = S_i / |J_i| in mode 0, S_i in mode 1, which they
+// multiply by alpha_ij), so that a sweep reads it with the slot's other
+// inputs instead of gathering it per variable.
+template <bool RENORM, bool SCATTER>
 __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __restrict__ M, float* lam,
                                                    const float* __restrict__ alpha, int mode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -32,12 +36,22 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
 #pragma unroll
     for (int r = 0; r < kEll; ++r)
       if (q[r] >= 0) s += mv[r];
+    int b = 0, e = 0;
     if (more) {
-      const int e = __ldg(A.var_ptr + i + 1);
-      for (int k = __ldg(A.var_ptr + i) + kEll; k < e; ++k) s += M[__ldg(A.var_slots + k)];
+      b = __ldg(A.var_ptr + i) + kEll;
+      e = __ldg(A.var_ptr + i + 1);
+      for (int k = b; k < e; ++k) s += M[__ldg(A.var_slots + k)];
     }
+    const float sbar = __ldg(A.invdeg + i) * s;
     A.S[i] = s;
-    A.Sbar[i] = __ldg(A.invdeg + i) * s;
+    A.Sbar[i] = sbar;
+    if (SCATTER) {
+      const float t = mode == 1 ? s : sbar;
+#pragma unroll
+      for (int r = 0; r < kEll; ++r)
+        if (q[r] >= 0) A.slot_avg[q[r]] = t;
+      for (int k = b; k < e; ++k) A.slot_avg[__ldg(A.var_slots + k)] = t;
+    }
     return;
   }
   const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
@@ -48,15 +62,18 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
     s += mk;
     tot += (double)lam[q] + (double)mk;
   }
+  const float sbar = __ldg(A.invdeg + i) * s;
   A.S[i] = s;
-  A.Sbar[i] = __ldg(A.invdeg + i) * s;
+  A.Sbar[i] = sbar;
   if (e > b) {
     const double r = A.c[i] - tot;
     const float inv = __ldg(A.invdeg + i);
+    const float t = mode == 1 ? s : sbar;
     for (int k = b; k < e; ++k) {
       const int q = __ldg(A.var_slots + k);
       const double w = mode == 1 ? (double)alpha[q] : (double)inv;
       lam[q] = (float)((double)lam[q] + w * r);
+      if (SCATTER) A.slot_avg[q] = t;
     }
   }
 }
@@ -183,14 +200,16 @@ void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaS
 }
 
 void launch_reduce_S(const DevArena& A, const float* M, float* lam, const float* alpha, int mode, bool renorm,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool for_sweep) {
   const int T = 256;
   const int G = (A.n + T - 1) / T;
   if (G == 0) return;
   if (renorm)
-    k_reduce_S<true><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
+    for_sweep ? k_reduce_S<true, true><<<G, T, 0, st>>>(A, M, lam, alpha, mode)
+              : k_reduce_S<true, false><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
   else
-    k_reduce_S<false><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
+    for_sweep ? k_reduce_S<false, true><<<G, T, 0, st>>>(A, M, lam, alpha, mode)
+              : k_reduce_S<false, false><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
 }
 
 void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st) {

@@ -49,7 +49,6 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       lane_cost_to_top_rec(s, lane);
     else
       lane_cost_to_top(s, lane);
-    if (FWD) wait_gathers();
     if (desc_width(s.desc[lane]) > 0) DG_R(s, 2) = 0.0f;
     for (int h = 0; h < s.nh; ++h) {
       const uint32_t ds = s.desc[h * kWarp + lane];
@@ -147,7 +146,6 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       lane_cost_from_root_rec(s, lane);
     else
       lane_cost_from_root(s, lane);
-    wait_gathers();
     DG_W(s, kTopCode) = 0.0f;
     DG_W(s, kBotCode) = f_inf();
     for (int h = s.nh - 1; h >= 0; --h) {

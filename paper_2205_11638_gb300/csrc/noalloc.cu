@@ -84,6 +84,7 @@ dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, 
   A.E = reinterpret_cast<float*>(p);
   A.S = reinterpret_cast<float*>(p + bE);
   A.Sbar = reinterpret_cast<float*>(p + bE + bS);
+  A.slot_avg = nullptr;  // the bound's S reduction leaves the per-slot terms alone
   A.lb_part = reinterpret_cast<double*>(p + bE + 2 * bS);
   A.long_t = reinterpret_cast<float*>(p + bE + 2 * bS + bP);  // SP(., T) of the long BDDs' nodes
   A.long_d = nullptr;                                         // not read by the energy pass
@@ -91,7 +92,7 @@ dg_status lower_bound_noalloc(const DevArena& arena, const LaunchGroup* groups, 
   a.lam = const_cast<float*>(lam);
   a.E = A.E;
   launch_sweep(kEnergy, A, a, threads, groups, num_groups, ss);
-  launch_reduce_S(A, M, nullptr, nullptr, 0, false, st);
+  launch_reduce_S(A, M, nullptr, nullptr, 0, false, st, false);
   launch_lower_bound(A, lb, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DG_ECUDA, std::string("dg_lower_bound_noalloc: ") + cudaGetErrorString(e));

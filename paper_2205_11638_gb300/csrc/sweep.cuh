@@ -28,7 +28,7 @@ struct TileSmem {
   float* full;     // [32 * nmax] costs of the first pass (all levels), lane-interleaved
   float* ring;     // [32 * ring] costs of the sweep direction, two levels live
   float* lam;      // [32 * nh]
-  float* sg;       // [32 * nh] variable of the slot, then the gathered S term
+  float* sg;       // [32 * nh] averaging term of the slot's variable
   float* om;       // [32 * nh] omega_ij (mode 1)
   float* al;       // [32 * nh] alpha_ij (mode 1)
   uint16_t* desc;  // [32 * nh]
@@ -94,32 +94,20 @@ __device__ __forceinline__ uint32_t node_code(const TileSmem& s, int n, int lane
   return node_code(s.code, n, lane);
 }
 
-// L2 eviction priorities.  A sweep streams its tiles' arrays (child codes,
-// descriptors, lambda, ...) through L2 once, several times the L2's size,
-// while the per-variable terms it gathers (24 MB for 6 M variables) are hit
-// again and again at random: the streamed copies are marked evict_first and
-// the gathers evict_last, so the stream does not push the gathered array out.
+// L2 eviction priority of the staged tile arrays: a sweep streams them
+// through L2 once, several times the L2's size, so they are marked
+// evict_first and leave the lines the sweep writes (lambda and M, which the S
+// reduction after it reads) in place.
 __device__ __forceinline__ uint64_t l2_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
 
-// Asynchronous global -> shared copies (cp.async) with an L2 policy: 16 B for
-// the streamed tile arrays, 4 B for the gathers of per-variable terms.
+// Asynchronous 16-byte global -> shared copy (cp.async) with an L2 policy.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint64_t pol) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, uint64_t pol) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "l"(pol)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -133,10 +121,9 @@ __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes
 }
 
 // Warp-cooperative staging of the tile: child codes, slot descriptors,
-// lambda and (mode 1) omega and alpha, all by asynchronous copies.  With
-// WITH_S the per-variable averaging term (S_i / |J_i| in mode 0, S_i in
-// mode 1) of every slot is gathered too; those copies stay in flight until
-// wait_gathers(), so callers overlap them with the first min-sum pass.
+// lambda and, with WITH_S, the averaging term of every slot (A.slot_avg, as
+// the S reduction before the sweep left it) plus omega and alpha in mode 1,
+// all by asynchronous copies; returns once they have landed.
 template <bool WITH_S, int MODE>
 __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, TileSmem& s, const float* lam,
                                           const float* omega, const float* alpha, int lane) {
@@ -145,7 +132,7 @@ __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, Tile
   copy_async(s.desc, A.desc + T.slot_base, ns * 2, lane);
   copy_async(s.lam, lam + T.slot_base, ns * 4, lane);
   if (WITH_S) {
-    copy_async(s.sg, A.slot_var + T.slot_base, ns * 4, lane);
+    copy_async(s.sg, A.slot_avg + T.slot_base, ns * 4, lane);
     if (MODE == 1) {
       copy_async(s.om, omega + T.slot_base, ns * 4, lane);
       copy_async(s.al, alpha + T.slot_base, ns * 4, lane);
@@ -156,29 +143,9 @@ __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, Tile
   DG_F(s, kBotCode) = f_inf();
   cp_async_wait_all();
   __syncwarp();
-  if (WITH_S) {
-    const float* src = MODE == 1 ? A.S : A.Sbar;
-    int* sv = reinterpret_cast<int*>(s.sg);
-    const uint64_t pol = l2_evict_last();
-#pragma unroll 4
-    for (int q = lane; q < ns; q += kWarp) {
-      const int v = sv[q];
-      if (v >= 0)
-        cp_async4(s.sg + q, src + v, pol);
-      else
-        s.sg[q] = 0.0f;
-    }
-    cp_async_commit();
-  }
 }
 
-// Completes the gathers issued by load_tile<true>.
-__device__ __forceinline__ void wait_gathers() {
-  cp_async_wait_all();
-  __syncwarp();
-}
-
-// alpha_ij * S_i of slot q (after wait_gathers).
+// The term a sweep adds to lambda_ij of slot q: alpha_ij * S_i.
 template <int MODE>
 __device__ __forceinline__ float slot_avg(const TileSmem& s, int q) {
   return MODE == 1 ? s.al[q] * s.sg[q] : s.sg[q];
