@@ -700,8 +700,8 @@ void dg_graph_destroy(dg_graph_t* g) {
 namespace {
 
 struct BwdLayout {
-  size_t ck_lam, ck_M, rec_meta, rec_amin, rec_diff, seg_S, w_lam, w_M, sdot, sd_a, sd_b, rec_lmeta, rec_lamin,
-      long_a1, long_a2, total;
+  size_t ck_lam, ck_M, rec_meta, rec_amin, rec_diff, seg_S, w_lam, w_M, sdot, sd_a, sd_b, slot_in, rec_lmeta,
+      rec_lamin, long_a1, long_a2, total;
   size_t meta_stride;   // bytes of one sweep's node records
   size_t lmeta_stride;  // ... of the long BDDs' node records
   size_t lamin_stride;  // ... of the long BDDs' slot records
@@ -732,6 +732,7 @@ BwdLayout backward_layout(const dg_arena* ar, int iters, int ckpt_every) {
   L.sdot = put(NS * 4);
   L.sd_a = put(n * 4);
   L.sd_b = put(n * 4);
+  L.slot_in = put(NS * 16);  // float4 per slot: the adjoint sweep's per-variable inputs
   // long BDDs: node and slot records of every sweep of one segment, and the
   // per-node gradients of the adjoint
   const size_t lcost = (size_t)ar->dev.long_cost_size, lslots = NS - (size_t)ar->dev.long_slot_base;
@@ -850,6 +851,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   float* sdot = (float*)(w + L.sdot);
   float* sd_next = (float*)(w + L.sd_a);
   float* sd_cur = (float*)(w + L.sd_b);
+  float4* slot_in = (float4*)(w + L.slot_in);
   const int threads = threads_of(opts);
   SweepArgs fa{};
   fa.lam = w_lam;
@@ -896,6 +898,9 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   aa.g_omega = g_omega;
   aa.g_alpha = g_alpha;
   aa.sdot = sdot;
+  aa.slot_in = slot_in;
+  // padding slots belong to no variable: their inputs stay 0
+  if (e == cudaSuccess && iters > 0) e = cudaMemsetAsync(slot_in, 0, NS * 16, st);
   aa.long_a1 = (float*)(w + L.long_a1);
   aa.long_a2 = (float*)(w + L.long_a2);
   const int last_sweep = 2 * iters - 1;
@@ -919,6 +924,10 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads, ar->groups.data(), (int)ar->groups.size(),
                    streams_for(ar, st));
     }
+    // the per-slot inputs of the segment's last sweep: the S-dot handed over
+    // from the adjoint of the segment after it (none after the last sweep)
+    launch_slot_inputs(A, nullptr, 2 * it0 + nsw - 1 == last_sweep ? nullptr : sd_next, nullptr,
+                       seg_S + (size_t)(nsw - 1) * n, slot_in, st);
     for (int sw = nsw - 1; sw >= 0; --sw) {
       const int gsw = 2 * it0 + sw;
       aa.rec_meta = (const uint16_t*)(rec_meta + (size_t)sw * L.meta_stride);
@@ -931,7 +940,9 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       aa.sdot_next = gsw == last_sweep ? nullptr : sd_next;
       launch_adjoint_sweep(sw % 2 == 0, A, aa, ar->adj_groups.data(), (int)ar->adj_groups.size(), ar->cta_smem_cap,
                            streams_for(ar, st));
-      launch_reduce_slots(A, sdot, sd_cur, st);
+      // S-dot of this sweep, and the next adjoint sweep's per-slot inputs
+      launch_slot_inputs(A, sdot, nullptr, sd_cur, sw > 0 ? seg_S + (size_t)(sw - 1) * n : nullptr,
+                         sw > 0 ? slot_in : nullptr, st);
       std::swap(sd_next, sd_cur);
     }
   }

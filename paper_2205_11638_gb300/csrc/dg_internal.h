@@ -200,12 +200,12 @@ inline size_t sweep_smem_bytes_bwd(int nmax, int nhops, int mode) {
   return sweep_smem_bytes(nmax, nhops, mode, nmax);
 }
 // ... and in the adjoint kernels: two gradient arrays, the argmin record and
-// the child codes per node; per slot the descriptor, the lambda gradient and
-// the variable (the other per-slot inputs of the reverse are read into
-// registers a level ahead, the same in both modes).
+// the child codes per node; per slot the descriptor and the lambda gradient
+// (the other per-slot inputs of the reverse are read into registers a level
+// ahead, the same in both modes).
 inline size_t adjoint_smem_bytes(int nmax, int nhops) {
   const size_t nn = (size_t)nmax * kWarp, ns = (size_t)nhops * kWarp;
-  size_t b = nn * 10 + ns * 10 + (size_t)(nmax - 2) * kWarp * 2;
+  size_t b = nn * 10 + ns * 6 + (size_t)(nmax - 2) * kWarp * 2;
   return (b + 127) / 128 * 128;
 }
 

@@ -79,6 +79,11 @@ struct AdjArgs {
   int mode;
   const float* seed_M;     // nullable: gradient of the sweep's M output (per slot)
   const float* sdot_next;  // nullable: S-dot of the next sweep (per variable)
+  // per slot: {S-dot of the next sweep, S at the sweep's start, 1/|J_i|, 0}
+  // of the slot's variable (launch_slot_inputs), what the tiles' reverse
+  // reads instead of gathering per variable; the long BDDs use the
+  // per-variable arrays above
+  const float4* slot_in;
   float* g_lam;            // in: gradient of lambda after the sweep; out: before
   float* g_omega;          // accumulated
   float* g_alpha;          // accumulated
@@ -93,8 +98,12 @@ struct AdjArgs {
 cudaError_t set_adjoint_smem_limit(size_t bytes);
 void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, const AdjGroup* groups, int num_groups,
                           size_t cta_smem_cap, const StreamSet& ss);
-// out_var[i] = sum over the slots q of variable i of x[q] (fixed order)
-void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cudaStream_t st);
+// Per variable i: s_i = sum over the slots q of i of x[q] (fixed order), or
+// sd_in[i] when x is NULL (0 when both are); out_var[i] = s_i (nullable);
+// and, when slot_in is not NULL, slot_in[q] = {s_i, S_var[i] (0 if NULL),
+// 1/|J_i|, 0} for every slot q of i.
+void launch_slot_inputs(const DevArena& A, const float* x, const float* sd_in, float* out_var, const float* S_var,
+                        float4* slot_in, cudaStream_t st);
 // out_slot[q] = v[variable of q] (0 for padding slots)
 void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st);
 

@@ -30,7 +30,8 @@ namespace {
 // (S^in, alpha, omega, M-dot, the recorded argmins and m1 - m0, and the
 // running omega-dot / alpha-dot sums) are read from global memory into
 // registers one level ahead instead (see LevelIn), which keeps a tile's
-// footprint small enough for more warps per SM.
+// footprint small enough for more warps per SM; the per-variable ones come
+// laid out per slot (AdjArgs::slot_in), so no read depends on another.
 struct AdjSmem {
   float* a1;       // [32 * nmax] gradient of SP(., T)
   float* a2;       // [32 * nmax] gradient of SP(r, .)
@@ -38,7 +39,6 @@ struct AdjSmem {
   uint16_t* code;  // [32 * (nmax - 2)]
   uint16_t* desc;  // [32 * nh]
   float* gl;       // [32 * nh] lambda gradient (new -> old)
-  int* var;        // [32 * nh] variable of the slot (-1: padding)
   int nmax, nh;
 };
 
@@ -56,8 +56,6 @@ __device__ __forceinline__ AdjSmem carve_adj(unsigned char* p, const Tile& T) {
   s.a2 = (float*)p;
   p += (size_t)nn * 4;
   s.gl = (float*)p;
-  p += (size_t)ns * 4;
-  s.var = (int*)p;
   p += (size_t)ns * 4;
   s.meta = (uint16_t*)p;
   p += (size_t)nn * 2;
@@ -78,14 +76,14 @@ __device__ __forceinline__ LevelIn load_level(const DevArena& A, const AdjArgs& 
                                               int h, int lane) {
   LevelIn r;
   const int q = h * kWarp + lane;
-  const int v = s.var[q];
+  const float4 in = a.slot_in[sb + q];
   r.diff = a.rec_diff[sb + q];
   r.amin = a.rec_amin[sb + q];
-  r.S = v >= 0 ? a.S_in[v] : 0.0f;
-  r.al = MODE == 1 ? a.alpha[sb + q] : (v >= 0 ? __ldg(A.invdeg + v) : 0.0f);
+  r.S = in.y;
+  r.al = MODE == 1 ? a.alpha[sb + q] : in.z;
   r.om = MODE == 1 ? a.omega[sb + q] : a.omega0;
   const float seed = a.seed_M ? a.seed_M[sb + q] : 0.0f;
-  r.md = seed + ((a.sdot_next && v >= 0) ? a.sdot_next[v] : 0.0f);  // gradient of M^new
+  r.md = seed + in.x;  // gradient of M^new
   r.ga = a.g_alpha[sb + q];
   r.go = a.g_omega[sb + q];
   return r;
@@ -109,7 +107,6 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
   copy_async(s.meta + 2 * kWarp, a.rec_meta + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
   copy_async(s.desc, A.desc + sb, ns * 2, lane);
   copy_async(s.gl, a.g_lam + sb, ns * 4, lane);
-  copy_async(s.var, A.slot_var + sb, ns * 4, lane);
   cp_async_commit();
   // gradient accumulators of SP(., T) and SP(r, .)
   for (int n = 0; n < s.nmax; ++n) {

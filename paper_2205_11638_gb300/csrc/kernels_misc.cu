@@ -171,13 +171,24 @@ __global__ void k_seed_M(DevArena A, float* gM) {
   gM[q] = (var >= 0 && A.S[var] < 0.f) ? 1.f : 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_reduce_slots(DevArena A, const float* __restrict__ x, float* out) {
+// Between two adjoint sweeps: the S-dot of a variable (sum of its slots'
+// contributions) and the per-slot inputs of the next adjoint sweep.
+__global__ void __launch_bounds__(256) k_slot_inputs(DevArena A, const float* __restrict__ x,
+                                                      const float* __restrict__ sd_in, float* out_var,
+                                                      const float* __restrict__ S_var, float4* slot_in) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
   float s = 0.f;
-  for (int k = b; k < e; ++k) s += x[__ldg(A.var_slots + k)];
-  out[i] = s;
+  if (x)
+    for (int k = b; k < e; ++k) s += x[__ldg(A.var_slots + k)];
+  else if (sd_in)
+    s = sd_in[i];
+  if (out_var) out_var[i] = s;
+  if (slot_in) {
+    const float4 t = make_float4(s, S_var ? S_var[i] : 0.f, __ldg(A.invdeg + i), 0.f);
+    for (int k = b; k < e; ++k) slot_in[__ldg(A.var_slots + k)] = t;
+  }
 }
 
 __global__ void k_gather_var(DevArena A, const float* __restrict__ v, float* out) {
@@ -187,10 +198,11 @@ __global__ void k_gather_var(DevArena A, const float* __restrict__ v, float* out
   out[q] = var >= 0 ? v[var] : 0.f;
 }
 
-void launch_reduce_slots(const DevArena& A, const float* x, float* out_var, cudaStream_t st) {
+void launch_slot_inputs(const DevArena& A, const float* x, const float* sd_in, float* out_var, const float* S_var,
+                        float4* slot_in, cudaStream_t st) {
   const int T = 256;
   const int G = (A.n + T - 1) / T;
-  if (G > 0) k_reduce_slots<<<G, T, 0, st>>>(A, x, out_var);
+  if (G > 0) k_slot_inputs<<<G, T, 0, st>>>(A, x, sd_in, out_var, S_var, slot_in);
 }
 
 void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st) {
