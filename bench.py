@@ -436,11 +436,11 @@ def _long_rows_measurement(solver, torch, iters=50, reps=3):
         sw = []
         for r in range(4):
             ev[0].record(stream)
-            A.sweep(lam, M, forward=True, stream=stream)
+            A.sweep(lam, M, forward=True, stream=stream, costs_out=True)
             ev[1].record(stream)
             A.sum_M(M, stream=stream)
             ev[2].record(stream)
-            A.sweep(lam, M, forward=False, stream=stream)
+            A.sweep(lam, M, forward=False, stream=stream, costs_in=True)
             ev[3].record(stream)
             ev[3].synchronize()
             if r > 0:
@@ -509,9 +509,9 @@ def _e2e_steps(A, lam, M, steps, stream, torch, chunks=4):
             stream.wait_event(ev_up[0])
             A.sum_M(d[0], stream=stream)
             stream.wait_event(ev_up[1])
-            A.sweep(d[1], d[0], forward=True, stream=stream)
+            A.sweep(d[1], d[0], forward=True, stream=stream, costs_out=True)
             A.sum_M(d[0], stream=stream)
-            A.sweep(d[1], d[0], forward=False, energy=True, stream=stream)
+            A.sweep(d[1], d[0], forward=False, energy=True, stream=stream, costs_in=True)
             ev_final.record(stream)
             s_down.wait_event(ev_final)
             for j in range(2):
@@ -720,13 +720,13 @@ def run_ours(args):
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        A.sweep(lam, M, forward=True)
+        A.sweep(lam, M, forward=True, costs_out=True)  # as dg_iterate: SP(r, .) handed on
         if ev is not None:
             ev[1].record(stream)
         A.sum_M(M)
         if ev is not None:
             ev[2].record(stream)
-        A.sweep(lam, M, forward=False, energy=True)
+        A.sweep(lam, M, forward=False, energy=True, costs_in=True)
         if ev is not None:
             ev[3].record(stream)
         A.sum_M(M)

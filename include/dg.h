@@ -214,15 +214,29 @@ dg_status dg_iterate(dg_arena* arena, void* stream, float* lam, float* M, const 
  * Alg. 1 (forward != 0: blocks B_1..B_u, else B_u..B_1) with that snapshot,
  * in the mode of the arena's last dg_sum_M (or S reduction of another call
  * that sweeps: dg_iterate, the checkpointed calls, dg_autotune in mode 0),
- * else DG_EINVAL; with want_energy (backward sweeps only) it also stores
- * E^j(lambda) of every row in the arena.  dg_bound_from_energies writes the
- * per-instance lower bound from the stored E and S (float64[num_inst]).
- * dg_iterate(iters) = dg_sum_M, then per iteration: dg_sweep(forward),
- * dg_sum_M, dg_sweep(backward), dg_sum_M. */
+ * else DG_EINVAL.  flags:
+ *   DG_SWEEP_ENERGY (backward sweeps only): also store E^j(lambda) of every
+ *     row in the arena;
+ *   DG_SWEEP_COSTS_OUT (forward sweeps only): leave SP(r, v) of every node
+ *     under the outgoing lambda (App. B's root-side recursion, which the
+ *     forward sweep computes anyway) in the arena;
+ *   DG_SWEEP_COSTS_IN (backward sweeps only): take SP(r, v) under the
+ *     incoming lambda from there instead of recomputing it.  Allowed only
+ *     when the arena's previous call was a forward dg_sweep with
+ *     DG_SWEEP_COSTS_OUT on the same lam (a dg_sum_M without renorm may run
+ *     in between), else DG_EINVAL; the caller must not have changed lam
+ *     since.  The results are bit for bit those of the sweep without it.
+ * dg_bound_from_energies writes the per-instance lower bound from the stored
+ * E and S (float64[num_inst]).  dg_iterate(iters) = dg_sum_M, then per
+ * iteration: dg_sweep(forward, DG_SWEEP_COSTS_OUT), dg_sum_M,
+ * dg_sweep(backward, DG_SWEEP_COSTS_IN), dg_sum_M. */
+#define DG_SWEEP_ENERGY 1
+#define DG_SWEEP_COSTS_OUT 2
+#define DG_SWEEP_COSTS_IN 4
 dg_status dg_sum_M(dg_arena* arena, void* stream, const float* M, float* lam, const float* alpha, int32_t mode,
                    int32_t renorm);
 dg_status dg_sweep(dg_arena* arena, void* stream, float* lam, float* M, const float* omega, const float* alpha,
-                   int32_t mode, int32_t forward, int32_t want_energy, const dg_options* opts);
+                   int32_t mode, int32_t forward, int32_t flags, const dg_options* opts);
 dg_status dg_bound_from_energies(dg_arena* arena, void* stream, double* lb_out);
 
 /* Min-marginals m0, m1 of every slot under lam (no update): for slot (i,j),

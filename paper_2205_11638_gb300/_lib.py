@@ -20,6 +20,7 @@ c_float = ctypes.c_float
 c_double = ctypes.c_double
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EINFEASIBLE, DG_EFORCED, DG_ETIMEOUT, DG_ESTATE = range(8)
+DG_SWEEP_ENERGY, DG_SWEEP_COSTS_OUT, DG_SWEEP_COSTS_IN = 1, 2, 4  # dg_sweep flags
 STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EINFEASIBLE",
                 5: "DG_EFORCED", 6: "DG_ETIMEOUT", 7: "DG_ESTATE"}
 

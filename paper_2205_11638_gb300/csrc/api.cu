@@ -41,6 +41,12 @@ struct dg_arena_s {
   // mode of the averaging terms the last S reduction for a sweep wrote into
   // the per-slot array (-1: none yet, the array holds zeros)
   int avg_mode = -1;
+  // SP(r, .) handed from a dg_sweep forward to the backward one after it
+  // (DG_SWEEP_COSTS_*): every API call advances `epoch`; the forward sweep
+  // that wrote the costs records its epoch and lambda, and only dg_sum_M
+  // without re-projection may run in between
+  uint64_t epoch = 0, costs_epoch = 0;
+  const float* costs_lam = nullptr;
 };
 
 struct dg_graph_s {
@@ -87,10 +93,16 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   ar->avg_mode = mode;
   launch_reduce_S(A, M, lam, alpha, mode, false, st, true);
   for (int it = 0; it < iters; ++it) {
+    // the forward sweep hands SP(r, .) to the backward sweep (the S
+    // reduction between them leaves lambda alone)
     a.E = nullptr;
+    a.cost_out = A.nodecost;
+    a.cost_in = nullptr;
     launch_sweep(kFwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     launch_reduce_S(A, M, lam, alpha, mode, false, st, true);
     if (lb_out && it == iters - 1) a.E = A.E;
+    a.cost_out = nullptr;
+    a.cost_in = A.nodecost;
     launch_sweep(kBwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
     launch_reduce_S(A, M, lam, alpha, mode, rn, st, it + 1 < iters);
@@ -122,6 +134,7 @@ bool missing(const dg_arena* ar, const void* p) { return p == nullptr && ar->siz
 
 dg_status check_state(const dg_arena* ar) {
   if (!ar) return fail(DG_ESTATE, "null arena");
+  ++const_cast<dg_arena*>(ar)->epoch;
   return DG_OK;
 }
 
@@ -340,6 +353,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.long_in = (const int32_t*)(b + P.off.long_in);
   A.long_d = (float*)(b + P.off.long_d);
   A.long_t = (float*)(b + P.off.long_t);
+  A.nodecost = (float*)(b + P.off.nodecost);
   A.S = (float*)(b + P.off.S);
   A.Sbar = (float*)(b + P.off.Sbar);
   A.slot_avg = (float*)(b + P.off.slot_avg);
@@ -446,9 +460,13 @@ dg_status dg_autotune(dg_arena* ar, void* stream, float* lam, float* M, int32_t 
   };
   ar->avg_mode = 0;
   launch_reduce_S(A, M, nullptr, nullptr, 0, false, st, true);
+  // timed as dg_iterate runs them: SP(r, .) handed from forward to backward
   auto pair = [&] {
-    launch_sweep(kFwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
-    launch_sweep(kBwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+    SweepArgs f = a, b = a;
+    f.cost_out = A.nodecost;
+    b.cost_in = A.nodecost;
+    launch_sweep(kFwd, A, f, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+    launch_sweep(kBwd, A, b, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
   };
   // start from the occupancy choice, made explicit
   for (LaunchGroup& G : ar->groups) {
@@ -516,17 +534,29 @@ dg_status dg_sum_M(dg_arena* ar, void* stream, const float* M, float* lam, const
   if (!M || (renorm && !lam)) return fail(DG_EINVAL, "dg_sum_M: null pointer");
   if (renorm && mode == 1 && !alpha) return fail(DG_EINVAL, "dg_sum_M: mode 1 needs alpha");
   ar->avg_mode = mode;
+  // a reduction without re-projection leaves lambda, so a hand-off survives it
+  if (!renorm && ar->costs_epoch + 1 == ar->epoch) ar->costs_epoch = ar->epoch;
   launch_reduce_S(ar->dev, M, lam, alpha, mode, renorm != 0, (cudaStream_t)stream, true);
   return check_launch("dg_sum_M");
 }
 
 dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float* omega, const float* alpha,
-                   int32_t mode, int32_t forward, int32_t want_energy, const dg_options* opts) {
+                   int32_t mode, int32_t forward, int32_t flags, const dg_options* opts) {
   if (dg_status s = check_state(ar)) return s;
   if (missing(ar, lam) || missing(ar, M)) return fail(DG_EINVAL, "dg_sweep: null state");
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_sweep: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_sweep: mode 1 needs omega and alpha");
+  if (flags & ~(DG_SWEEP_ENERGY | DG_SWEEP_COSTS_OUT | DG_SWEEP_COSTS_IN))
+    return fail(DG_EINVAL, "dg_sweep: unknown flag");
+  const bool want_energy = (flags & DG_SWEEP_ENERGY) != 0;
   if (forward && want_energy) return fail(DG_EINVAL, "dg_sweep: energies come from backward sweeps");
+  if (forward && (flags & DG_SWEEP_COSTS_IN))
+    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_IN is for backward sweeps");
+  if (!forward && (flags & DG_SWEEP_COSTS_OUT))
+    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_OUT is for forward sweeps");
+  if ((flags & DG_SWEEP_COSTS_IN) && (ar->costs_epoch + 1 != ar->epoch || ar->costs_lam != lam))
+    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_IN needs the arena's previous call to be a forward sweep on the "
+                           "same lambda with DG_SWEEP_COSTS_OUT (only dg_sum_M without renorm may run in between)");
   if (ar->avg_mode >= 0 && ar->avg_mode != mode)
     return fail(DG_EINVAL, "dg_sweep: mode differs from the one the arena's last S reduction (dg_sum_M) was run in");
   if (dg_status s = check_vectors("dg_sweep", lam, M, omega, alpha)) return s;
@@ -538,8 +568,14 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
   a.omega0 = omega_of(opts);
   a.mode = mode;
   a.E = want_energy ? ar->dev.E : nullptr;
+  a.cost_out = (flags & DG_SWEEP_COSTS_OUT) ? ar->dev.nodecost : nullptr;
+  a.cost_in = (flags & DG_SWEEP_COSTS_IN) ? ar->dev.nodecost : nullptr;
   launch_sweep(forward ? kFwd : kBwd, ar->dev, a, threads_of(opts), ar->groups.data(), (int)ar->groups.size(),
                streams_for(ar, (cudaStream_t)stream));
+  if (flags & DG_SWEEP_COSTS_OUT) {
+    ar->costs_epoch = ar->epoch;
+    ar->costs_lam = lam;
+  }
   return check_launch("dg_sweep");
 }
 
@@ -878,10 +914,13 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       break;
     }
     for (int it = 0; it < L.k; ++it) {
+      SweepArgs f = fa, b = fa;  // SP(r, .) handed from forward to backward, as in dg_iterate
+      f.cost_out = A.nodecost;
+      b.cost_in = A.nodecost;
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);
-      launch_sweep(kFwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+      launch_sweep(kFwd, A, f, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);
-      launch_sweep(kBwd, A, fa, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+      launch_sweep(kBwd, A, b, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     }
   }
   // 2. segments newest first: recompute every sweep of the segment as a

@@ -20,6 +20,14 @@ struct SweepArgs {
   float omega0;        // mode 0
   int mode;
   float* E;            // nullable: E^j per original row (kBwd, kEnergy)
+  // Hand-off of SP(r, .) from a forward sweep to the backward sweep after it
+  // (per node and lane of the tiles, in the layout of the child codes; both
+  // nullable).  kFwd with cost_out: writes SP(r, .) under the outgoing
+  // lambda, which it computes anyway.  kBwd with cost_in: reads SP(r, .)
+  // under its incoming lambda from there instead of recomputing it, valid
+  // when lambda has not changed since that forward sweep.
+  float* cost_out;
+  const float* cost_in;
   // argmin records (kFwdRec, kBwdRec), read back by the adjoint of the sweep:
   uint16_t* rec_meta;  // per node (layout of the child codes): in-arc parent | beta << 8 | hi-choice << 9
   uint16_t* rec_amin;  // per slot: argmin node of m0 | argmin node of m1 << 8

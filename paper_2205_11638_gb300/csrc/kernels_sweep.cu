@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
   if (tile >= tile1) return;  // whole warp leaves; no CTA-wide barrier follows
   const Tile T = A.tiles[tile];
   TileSmem s = carve<MODE, !BWD, REC>(smem + (size_t)warp * region_bytes, T);
-  load_tile<FWD || BWD, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane);
+  // a plain backward sweep may take SP(r, .) from the forward sweep before it
+  const float* cost_in = KIND == kBwd ? a.cost_in : nullptr;
+  load_tile<FWD || BWD, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane, cost_in);
   const int64_t sbase = T.slot_base;
 
   if (FWD || KIND == kMinMarg) {
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         if (i < w) {
           cc[i] = node_code(s, fn + i, lane);
           dd[i] = DG_R(s, fn + i);
+          if (KIND == kFwd) DG_F(s, fn + i) = dd[i];
           b0 = fminf(b0, dd[i] + DG_F(s, cc[i] & 0xFFu));
           b1 = fminf(b1, dd[i] + DG_F(s, cc[i] >> 8));
         }
@@ -81,6 +84,9 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         const uint32_t c = node_code(s, n, lane);
         const float dv = DG_R(s, n);
         const float x0 = dv + DG_F(s, c & 0xFFu), x1 = dv + DG_F(s, c >> 8);
+        // SP(r, n) is final here and SP(n, T) is not read again: the whole
+        // array ends the sweep holding SP(r, .) under the new lambda
+        if (KIND == kFwd) DG_F(s, n) = dv;
         if (REC) {
           if (x0 < b0) { b0 = x0; v0 = n; }
           if (x1 < b1) { b1 = x1; v1 = n; }
@@ -140,11 +146,12 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         }
       }
     }
+    if (KIND == kFwd && a.cost_out) store_costs(a.cost_out + T.node_base, s.full, s.nmax, lane);
   } else if (BWD) {
     // ---- SP(r, .) under lambda at sweep start, then the backward sweep ----
     if (REC)
       lane_cost_from_root_rec(s, lane);
-    else
+    else if (!cost_in)
       lane_cost_from_root(s, lane);
     DG_W(s, kTopCode) = 0.0f;
     DG_W(s, kBotCode) = f_inf();

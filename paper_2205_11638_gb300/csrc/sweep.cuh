@@ -123,12 +123,16 @@ __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes
 // Warp-cooperative staging of the tile: child codes, slot descriptors,
 // lambda and, with WITH_S, the averaging term of every slot (A.slot_avg, as
 // the S reduction before the sweep left it) plus omega and alpha in mode 1,
-// all by asynchronous copies; returns once they have landed.
+// all by asynchronous copies; returns once they have landed.  With costs
+// non-null, the costs of nodes 2 .. nmax-1 (per node and lane, in the layout
+// of the child codes) are staged into s.full as well.
 template <bool WITH_S, int MODE>
 __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, TileSmem& s, const float* lam,
-                                          const float* omega, const float* alpha, int lane) {
+                                          const float* omega, const float* alpha, int lane,
+                                          const float* costs = nullptr) {
   const int ns = s.nh * kWarp;
   copy_async(s.code_base, A.lohi8 + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+  if (costs) copy_async(s.full + 2 * kWarp, costs + T.node_base, (s.nmax - 2) * kWarp * 4, lane);
   copy_async(s.desc, A.desc + T.slot_base, ns * 2, lane);
   copy_async(s.lam, lam + T.slot_base, ns * 4, lane);
   if (WITH_S) {
@@ -143,6 +147,26 @@ __device__ __forceinline__ void load_tile(const DevArena& A, const Tile& T, Tile
   DG_F(s, kBotCode) = f_inf();
   cp_async_wait_all();
   __syncwarp();
+}
+
+// Writes the costs of nodes 2 .. nmax-1 held in `src` (a lane-interleaved
+// cost array of the tile's shared memory) to dst, in the layout load_tile
+// reads them back in: one bulk asynchronous copy (TMA engine) issued by lane
+// 0, which waits for its completion before the warp's shared memory can go.
+// Both addresses are 16-byte aligned (slices start on 128 bytes, node_base
+// is a multiple of 32) and the size is a multiple of 128 bytes.
+__device__ __forceinline__ void store_costs(float* dst, const float* src, int nmax, int lane) {
+  // the lanes' shared-memory stores, ordered before the async proxy reads them
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(src + 2 * kWarp);
+    const unsigned bytes = (unsigned)(nmax - 2) * kWarp * 4u;
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(s), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
 }
 
 // The term a sweep adds to lambda_ij of slot q: alpha_ij * S_i.

@@ -219,10 +219,14 @@ class Arena:
         check(_lib.load().dg_sum_M(self._h, _stream_handle(stream), _ptr(M), _ptr(lam), _ptr(alpha), mode,
                                    int(bool(renorm))), "dg_sum_M")
 
-    def sweep(self, lam, M, forward, omega=None, alpha=None, energy=False, stream=None):
+    def sweep(self, lam, M, forward, omega=None, alpha=None, energy=False, stream=None, costs_out=False,
+              costs_in=False):
+        """dg_sweep; costs_out / costs_in are DG_SWEEP_COSTS_OUT (forward) / DG_SWEEP_COSTS_IN (backward)."""
         mode = 0 if omega is None else 1
+        flags = (_lib.DG_SWEEP_ENERGY if energy else 0) | (_lib.DG_SWEEP_COSTS_OUT if costs_out else 0) | \
+            (_lib.DG_SWEEP_COSTS_IN if costs_in else 0)
         check(_lib.load().dg_sweep(self._h, _stream_handle(stream), _ptr(lam), _ptr(M), _ptr(omega), _ptr(alpha),
-                                   mode, int(bool(forward)), int(bool(energy)), ctypes.byref(self.options)),
+                                   mode, int(bool(forward)), flags, ctypes.byref(self.options)),
               "dg_sweep")
 
     def bound_from_energies(self, lb_out, stream=None):
