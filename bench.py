@@ -436,11 +436,11 @@ def _long_rows_measurement(solver, torch, iters=50, reps=3):
         sw = []
         for r in range(4):
             ev[0].record(stream)
-            A.sweep(lam, M, forward=True, stream=stream, costs_out=True)
+            A.sweep(lam, M, forward=True, stream=stream, costs_in=r > 0, costs_out=True)
             ev[1].record(stream)
             A.sum_M(M, stream=stream)
             ev[2].record(stream)
-            A.sweep(lam, M, forward=False, stream=stream, costs_in=True)
+            A.sweep(lam, M, forward=False, stream=stream, costs_in=True, costs_out=True)
             ev[3].record(stream)
             ev[3].synchronize()
             if r > 0:
@@ -717,22 +717,27 @@ def run_ours(args):
     lam, M = A.init_lambda()
     lb_out = torch.zeros(A.num_inst, dtype=torch.float64, device=A.device)
 
+    # the steps run as dg_iterate does: every sweep takes the path costs the
+    # sweep before it left (except the very first)
+    handed = [False]
+
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        A.sweep(lam, M, forward=True, costs_out=True)  # as dg_iterate: SP(r, .) handed on
+        A.sweep(lam, M, forward=True, costs_in=handed[0], costs_out=True)
         if ev is not None:
             ev[1].record(stream)
         A.sum_M(M)
         if ev is not None:
             ev[2].record(stream)
-        A.sweep(lam, M, forward=False, energy=True, costs_in=True)
+        A.sweep(lam, M, forward=False, energy=True, costs_in=True, costs_out=True)
         if ev is not None:
             ev[3].record(stream)
         A.sum_M(M)
         A.bound_from_energies(lb_out)
         if ev is not None:
             ev[4].record(stream)
+        handed[0] = True
 
     A.sum_M(M)
     for _ in range(args.warmup):

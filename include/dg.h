@@ -217,19 +217,22 @@ dg_status dg_iterate(dg_arena* arena, void* stream, float* lam, float* M, const 
  * else DG_EINVAL.  flags:
  *   DG_SWEEP_ENERGY (backward sweeps only): also store E^j(lambda) of every
  *     row in the arena;
- *   DG_SWEEP_COSTS_OUT (forward sweeps only): leave SP(r, v) of every node
- *     under the outgoing lambda (App. B's root-side recursion, which the
- *     forward sweep computes anyway) in the arena;
- *   DG_SWEEP_COSTS_IN (backward sweeps only): take SP(r, v) under the
- *     incoming lambda from there instead of recomputing it.  Allowed only
- *     when the arena's previous call was a forward dg_sweep with
- *     DG_SWEEP_COSTS_OUT on the same lam (a dg_sum_M without renorm may run
- *     in between), else DG_EINVAL; the caller must not have changed lam
- *     since.  The results are bit for bit those of the sweep without it.
+ *   DG_SWEEP_COSTS_OUT: leave the path costs of the sweep's own direction
+ *     under the outgoing lambda, which the sweep computes anyway, in the
+ *     arena (App. B's two recursions: SP(r, v) after a forward sweep,
+ *     SP(v, T) after a backward one);
+ *   DG_SWEEP_COSTS_IN: take the costs opposite to the sweep's direction under
+ *     the incoming lambda from there instead of recomputing them.  Allowed
+ *     only when the arena's previous call was a sweep in the other direction
+ *     with DG_SWEEP_COSTS_OUT on the same lam (dg_sum_M without renorm and
+ *     dg_bound_from_energies may run in between), else DG_EINVAL; the caller
+ *     must not have changed lam since.  The results are bit for bit those of
+ *     the sweep without it.
  * dg_bound_from_energies writes the per-instance lower bound from the stored
  * E and S (float64[num_inst]).  dg_iterate(iters) = dg_sum_M, then per
- * iteration: dg_sweep(forward, DG_SWEEP_COSTS_OUT), dg_sum_M,
- * dg_sweep(backward, DG_SWEEP_COSTS_IN), dg_sum_M. */
+ * iteration: dg_sweep(forward), dg_sum_M, dg_sweep(backward), dg_sum_M, with
+ * the costs handed on from every sweep to the next except into the first
+ * sweep and across a re-projection. */
 #define DG_SWEEP_ENERGY 1
 #define DG_SWEEP_COSTS_OUT 2
 #define DG_SWEEP_COSTS_IN 4

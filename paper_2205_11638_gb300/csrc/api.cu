@@ -41,11 +41,12 @@ struct dg_arena_s {
   // mode of the averaging terms the last S reduction for a sweep wrote into
   // the per-slot array (-1: none yet, the array holds zeros)
   int avg_mode = -1;
-  // SP(r, .) handed from a dg_sweep forward to the backward one after it
-  // (DG_SWEEP_COSTS_*): every API call advances `epoch`; the forward sweep
-  // that wrote the costs records its epoch and lambda, and only dg_sum_M
-  // without re-projection may run in between
+  // path costs handed from one dg_sweep to the next (DG_SWEEP_COSTS_*): every
+  // API call advances `epoch`; the sweep that wrote the costs records its
+  // epoch, direction and lambda, and only dg_sum_M without re-projection and
+  // dg_bound_from_energies may run in between
   uint64_t epoch = 0, costs_epoch = 0;
+  int costs_dir = -1;  // 1 forward, 0 backward
   const float* costs_lam = nullptr;
 };
 
@@ -92,19 +93,22 @@ dg_status enqueue_iterate(dg_arena* ar, cudaStream_t st, float* lam, float* M, c
   a.mode = mode;
   ar->avg_mode = mode;
   launch_reduce_S(A, M, lam, alpha, mode, false, st, true);
+  // every sweep hands its path costs to the next one (the S reductions
+  // between them leave lambda alone), except into the first sweep, whose
+  // lambda comes from the caller, and across a re-projection
+  bool handed = false;
   for (int it = 0; it < iters; ++it) {
-    // the forward sweep hands SP(r, .) to the backward sweep (the S
-    // reduction between them leaves lambda alone)
+    const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
     a.E = nullptr;
     a.cost_out = A.nodecost;
-    a.cost_in = nullptr;
+    a.cost_in = handed ? A.nodecost : nullptr;
     launch_sweep(kFwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
     launch_reduce_S(A, M, lam, alpha, mode, false, st, true);
     if (lb_out && it == iters - 1) a.E = A.E;
-    a.cost_out = nullptr;
+    handed = it + 1 < iters && !rn;
+    a.cost_out = handed ? A.nodecost : nullptr;
     a.cost_in = A.nodecost;
     launch_sweep(kBwd, A, a, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
-    const bool rn = renorm > 0 && ((it + 1) % renorm == 0);
     launch_reduce_S(A, M, lam, alpha, mode, rn, st, it + 1 < iters);
   }
   if (lb_out) {
@@ -136,6 +140,11 @@ dg_status check_state(const dg_arena* ar) {
   if (!ar) return fail(DG_ESTATE, "null arena");
   ++const_cast<dg_arena*>(ar)->epoch;
   return DG_OK;
+}
+
+// For the calls that leave lambda and the arena's handed-on path costs alone.
+void keep_costs(dg_arena* ar) {
+  if (ar->costs_epoch + 1 == ar->epoch) ar->costs_epoch = ar->epoch;
 }
 
 // Arena-order vectors are read and written as float4: 16-byte alignment.
@@ -460,13 +469,15 @@ dg_status dg_autotune(dg_arena* ar, void* stream, float* lam, float* M, int32_t 
   };
   ar->avg_mode = 0;
   launch_reduce_S(A, M, nullptr, nullptr, 0, false, st, true);
-  // timed as dg_iterate runs them: SP(r, .) handed from forward to backward
+  // timed as dg_iterate runs them after its first sweep: each sweep takes
+  // its opposite-direction costs from the one before
+  a.cost_out = A.nodecost;
+  launch_sweep(kFwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+  a.cost_in = A.nodecost;
+  launch_sweep(kBwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
   auto pair = [&] {
-    SweepArgs f = a, b = a;
-    f.cost_out = A.nodecost;
-    b.cost_in = A.nodecost;
-    launch_sweep(kFwd, A, f, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
-    launch_sweep(kBwd, A, b, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+    launch_sweep(kFwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
+    launch_sweep(kBwd, A, a, 128, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
   };
   // start from the occupancy choice, made explicit
   for (LaunchGroup& G : ar->groups) {
@@ -535,7 +546,7 @@ dg_status dg_sum_M(dg_arena* ar, void* stream, const float* M, float* lam, const
   if (renorm && mode == 1 && !alpha) return fail(DG_EINVAL, "dg_sum_M: mode 1 needs alpha");
   ar->avg_mode = mode;
   // a reduction without re-projection leaves lambda, so a hand-off survives it
-  if (!renorm && ar->costs_epoch + 1 == ar->epoch) ar->costs_epoch = ar->epoch;
+  if (!renorm) keep_costs(ar);
   launch_reduce_S(ar->dev, M, lam, alpha, mode, renorm != 0, (cudaStream_t)stream, true);
   return check_launch("dg_sum_M");
 }
@@ -550,13 +561,12 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
     return fail(DG_EINVAL, "dg_sweep: unknown flag");
   const bool want_energy = (flags & DG_SWEEP_ENERGY) != 0;
   if (forward && want_energy) return fail(DG_EINVAL, "dg_sweep: energies come from backward sweeps");
-  if (forward && (flags & DG_SWEEP_COSTS_IN))
-    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_IN is for backward sweeps");
-  if (!forward && (flags & DG_SWEEP_COSTS_OUT))
-    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_OUT is for forward sweeps");
-  if ((flags & DG_SWEEP_COSTS_IN) && (ar->costs_epoch + 1 != ar->epoch || ar->costs_lam != lam))
-    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_IN needs the arena's previous call to be a forward sweep on the "
-                           "same lambda with DG_SWEEP_COSTS_OUT (only dg_sum_M without renorm may run in between)");
+  const int dir = forward ? 1 : 0;
+  if ((flags & DG_SWEEP_COSTS_IN) &&
+      (ar->costs_epoch + 1 != ar->epoch || ar->costs_dir != 1 - dir || ar->costs_lam != lam))
+    return fail(DG_EINVAL, "dg_sweep: DG_SWEEP_COSTS_IN needs the arena's previous call to be a sweep in the other "
+                           "direction on the same lambda with DG_SWEEP_COSTS_OUT (only dg_sum_M without renorm and "
+                           "dg_bound_from_energies may run in between)");
   if (ar->avg_mode >= 0 && ar->avg_mode != mode)
     return fail(DG_EINVAL, "dg_sweep: mode differs from the one the arena's last S reduction (dg_sum_M) was run in");
   if (dg_status s = check_vectors("dg_sweep", lam, M, omega, alpha)) return s;
@@ -574,6 +584,7 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
                streams_for(ar, (cudaStream_t)stream));
   if (flags & DG_SWEEP_COSTS_OUT) {
     ar->costs_epoch = ar->epoch;
+    ar->costs_dir = dir;
     ar->costs_lam = lam;
   }
   return check_launch("dg_sweep");
@@ -582,6 +593,7 @@ dg_status dg_sweep(dg_arena* ar, void* stream, float* lam, float* M, const float
 dg_status dg_bound_from_energies(dg_arena* ar, void* stream, double* lb_out) {
   if (dg_status s = check_state(ar)) return s;
   if (!lb_out) return fail(DG_EINVAL, "dg_bound_from_energies: null output");
+  keep_costs(ar);
   launch_lower_bound(ar->dev, lb_out, (cudaStream_t)stream);
   return check_launch("dg_bound_from_energies");
 }
@@ -902,6 +914,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
     cpy(w_lam, lam0, bNS);
     cpy(w_M, M0, bNS);
   }
+  bool handed = false;  // the sweeps hand their path costs on as in dg_iterate
   for (int c = 0; c < (have_ckpt ? 0 : L.nseg); ++c) {
     cpy(ck_lam + (size_t)c * NS, w_lam, bNS);
     cpy(ck_M + (size_t)c * NS, w_M, bNS);
@@ -914,9 +927,11 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       break;
     }
     for (int it = 0; it < L.k; ++it) {
-      SweepArgs f = fa, b = fa;  // SP(r, .) handed from forward to backward, as in dg_iterate
-      f.cost_out = A.nodecost;
+      SweepArgs f = fa, b = fa;
+      f.cost_out = b.cost_out = A.nodecost;
+      f.cost_in = handed ? A.nodecost : nullptr;
       b.cost_in = A.nodecost;
+      handed = true;
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);
       launch_sweep(kFwd, A, f, threads, ar->groups.data(), (int)ar->groups.size(), streams_for(ar, st));
       launch_reduce_S(A, w_M, nullptr, nullptr, mode, false, st, true);

@@ -20,12 +20,16 @@ struct SweepArgs {
   float omega0;        // mode 0
   int mode;
   float* E;            // nullable: E^j per original row (kBwd, kEnergy)
-  // Hand-off of SP(r, .) from a forward sweep to the backward sweep after it
-  // (per node and lane of the tiles, in the layout of the child codes; both
-  // nullable).  kFwd with cost_out: writes SP(r, .) under the outgoing
-  // lambda, which it computes anyway.  kBwd with cost_in: reads SP(r, .)
-  // under its incoming lambda from there instead of recomputing it, valid
-  // when lambda has not changed since that forward sweep.
+  // Hand-off of App. B's path costs from one plain sweep to the next (per
+  // node and lane of the tiles, in the layout of the child codes; both
+  // nullable; kFwd / kBwd only).  cost_out: the costs of the sweep's own
+  // direction under the outgoing lambda, which it computes anyway (SP(r, .)
+  // after a forward sweep, SP(., T) after a backward one).  cost_in: the
+  // costs opposite to the sweep direction under the incoming lambda (SP(., T)
+  // for a forward sweep, SP(r, .) for a backward one), read instead of
+  // recomputed; valid when lambda has not changed since the sweep that wrote
+  // them.  The two may be the same array: each warp stages its tile's part
+  // before it writes it.
   float* cost_out;
   const float* cost_in;
   // argmin records (kFwdRec, kBwdRec), read back by the adjoint of the sweep:

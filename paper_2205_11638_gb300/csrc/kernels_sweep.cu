@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
   if (tile >= tile1) return;  // whole warp leaves; no CTA-wide barrier follows
   const Tile T = A.tiles[tile];
   TileSmem s = carve<MODE, !BWD, REC>(smem + (size_t)warp * region_bytes, T);
-  // a plain backward sweep may take SP(r, .) from the forward sweep before it
-  const float* cost_in = KIND == kBwd ? a.cost_in : nullptr;
+  // a plain sweep may take the opposite-direction costs from the sweep before it
+  const float* cost_in = (KIND == kFwd || KIND == kBwd) ? a.cost_in : nullptr;
   load_tile<FWD || BWD, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane, cost_in);
   const int64_t sbase = T.slot_base;
 
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
     // ---- SP(., T) under lambda at sweep start, then the forward sweep -----
     if (REC)
       lane_cost_to_top_rec(s, lane);
-    else
+    else if (!cost_in)
       lane_cost_to_top(s, lane);
     if (desc_width(s.desc[lane]) > 0) DG_R(s, 2) = 0.0f;
     for (int h = 0; h < s.nh; ++h) {
@@ -221,6 +221,8 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         }
       }
     }
+    // the second whole array ends the sweep holding SP(., T) under the new lambda
+    if (KIND == kBwd && a.cost_out) store_costs(a.cost_out + T.node_base, s.ring, s.nmax, lane);
   } else {
     // kEnergy / kSeed: SP(., T) under lambda
     lane_cost_to_top(s, lane);

@@ -221,7 +221,7 @@ class Arena:
 
     def sweep(self, lam, M, forward, omega=None, alpha=None, energy=False, stream=None, costs_out=False,
               costs_in=False):
-        """dg_sweep; costs_out / costs_in are DG_SWEEP_COSTS_OUT (forward) / DG_SWEEP_COSTS_IN (backward)."""
+        """dg_sweep; costs_out / costs_in are DG_SWEEP_COSTS_OUT / DG_SWEEP_COSTS_IN."""
         mode = 0 if omega is None else 1
         flags = (_lib.DG_SWEEP_ENERGY if energy else 0) | (_lib.DG_SWEEP_COSTS_OUT if costs_out else 0) | \
             (_lib.DG_SWEEP_COSTS_IN if costs_in else 0)

@@ -1,9 +1,9 @@
-"""SP(r, .) handed from a forward sweep to the backward sweep after it
-(DG_SWEEP_COSTS_OUT / DG_SWEEP_COSTS_IN, and dg_iterate's own hand-off): a
-backward sweep that reads App. B's root-side costs from the forward sweep
-instead of recomputing them must give bit for bit the lambda and M of the
-sweep that recomputes them, and the arena must refuse the hand-off whenever
-lambda may have changed in between."""
+"""Path costs handed from one sweep to the next (DG_SWEEP_COSTS_OUT /
+DG_SWEEP_COSTS_IN, and dg_iterate's own hand-off): a sweep that reads SP(., T)
+or SP(r, .) (App. B's two recursions) from the sweep before it instead of
+recomputing them must give bit for bit the lambda and M of the sweep that
+recomputes them, and the arena must refuse the hand-off whenever lambda may
+have changed in between."""
 import ctypes
 
 import numpy as np
@@ -38,12 +38,14 @@ def _mode1(prob, A, seed=3):
 def _manual(A, lam, M, iters, om=None, al=None, handoff=True, renorm_every=0):
     """dg_iterate's schedule spelled out with dg_sum_M / dg_sweep."""
     A.sum_M(M, alpha=al)
+    handed = False
     for it in range(iters):
         rn = renorm_every > 0 and (it + 1) % renorm_every == 0
-        A.sweep(lam, M, forward=True, omega=om, alpha=al, costs_out=handoff)
+        A.sweep(lam, M, forward=True, omega=om, alpha=al, costs_in=handoff and handed, costs_out=handoff)
         A.sum_M(M, alpha=al)
-        A.sweep(lam, M, forward=False, omega=om, alpha=al, costs_in=handoff)
+        A.sweep(lam, M, forward=False, omega=om, alpha=al, costs_in=handoff, costs_out=handoff and not rn)
         A.sum_M(M, lam=lam, alpha=al, renorm=rn)
+        handed = not rn
 
 
 def _free_random_rows(num, seed, n=500):
@@ -96,7 +98,7 @@ def test_renorm_iterations_bit_identical():
 
 def test_checkpoint_recompute_gradients_independent_of_interval():
     # the backward pass recomputes its checkpoints with plain sweeps that hand
-    # SP(r, .) on; gradients must not depend on the checkpoint interval
+    # their costs on; gradients must not depend on the checkpoint interval
     prob = workloads.tracking(frames=12, dets=200, seed=36)
     A = solver.plan(prob).bind()
     lam0, M0 = A.init_lambda()
@@ -127,8 +129,9 @@ def test_costs_in_refused_without_a_matching_costs_out():
 
     A.sum_M(M)
     refused(lambda: A.sweep(lam, M, forward=False, costs_in=True))            # nothing handed on yet
-    refused(lambda: A.sweep(lam, M, forward=True, costs_in=True), "backward sweeps")
-    refused(lambda: A.sweep(lam, M, forward=False, costs_out=True), "forward sweeps")
+    refused(lambda: A.sweep(lam, M, forward=True, costs_in=True))
+    A.sweep(lam, M, forward=True, costs_out=True)
+    refused(lambda: A.sweep(lam, M, forward=True, costs_in=True))             # same direction
     A.sweep(lam, M, forward=True, costs_out=True)
     refused(lambda: A.sweep(other, M, forward=False, costs_in=True))          # another lambda
     A.sweep(lam, M, forward=True, costs_out=True)
@@ -142,7 +145,11 @@ def test_costs_in_refused_without_a_matching_costs_out():
     refused(lambda: A.sweep(lam, M, forward=False, costs_in=True))            # a backward sweep in between
     A.sweep(lam, M, forward=True, costs_out=True)
     A.sum_M(M)
-    A.sweep(lam, M, forward=False, costs_in=True)                             # allowed
+    A.sweep(lam, M, forward=False, costs_in=True, costs_out=True)             # allowed
+    A.sum_M(M)
+    lb = torch.zeros(A.num_inst, dtype=torch.float64, device=A.device)
+    A.bound_from_energies(lb)
+    A.sweep(lam, M, forward=True, costs_in=True)                              # allowed
     torch.cuda.synchronize()
     assert torch.isfinite(lam).all()
     p = [ctypes.c_void_p(t.data_ptr()) for t in (lam, M)]
