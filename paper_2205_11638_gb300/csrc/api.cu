@@ -292,6 +292,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   cp(P.off.var_ptr, P.var_ptr.data(), P.var_ptr.size() * 4);
   cp(P.off.var_slots, P.var_slots.data(), P.var_slots.size() * 4);
   cp(P.off.var_ell, P.var_ell.data(), P.var_ell.size() * 4);
+  cp(P.off.wide_vars, P.wide_vars.data(), P.wide_vars.size() * 4);
   cp(P.off.c, P.c.data(), P.c.size() * 8);
   cp(P.off.invdeg, P.invdeg.data(), P.invdeg.size() * 4);
   cp(P.off.inst_row_ptr, P.inst_row_ptr.data(), P.inst_row_ptr.size() * 8);
@@ -348,6 +349,8 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.var_ptr = (const int32_t*)(b + P.off.var_ptr);
   A.var_slots = (const int32_t*)(b + P.off.var_slots);
   A.var_ell = (const int32_t*)(b + P.off.var_ell);
+  A.wide_vars = (const int32_t*)(b + P.off.wide_vars);
+  A.num_wide = (int32_t)P.wide_vars.size();
   A.c = (const double*)(b + P.off.c);
   A.invdeg = (const float*)(b + P.off.invdeg);
   A.inst_row_ptr = (const int64_t*)(b + P.off.inst_row_ptr);

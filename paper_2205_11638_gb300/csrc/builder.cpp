@@ -560,10 +560,12 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   }
   P.c.assign(R->c, R->c + n);
   P.var_ell.assign((size_t)kEll * n, -1);
+  P.wide_vars.clear();
   for (int32_t i = 0; i < n; ++i) {
     const int d = P.var_ptr[i + 1] - P.var_ptr[i];
     for (int r = 0; r < std::min(d, kEll); ++r) P.var_ell[(size_t)r * n + i] = P.var_slots[P.var_ptr[i] + r];
     if (d > kEll) P.var_ell[(size_t)(kEll - 1) * n + i] = -2 - P.var_ell[(size_t)(kEll - 1) * n + i];
+    if (d > kWide) P.wide_vars.push_back(i);
   }
   P.invdeg.assign(n, 0.0f);
   for (int32_t i = 0; i < n; ++i) {
@@ -607,6 +609,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.var_ptr = put((size_t)(n + 1) * 4);
   P.off.var_slots = put((size_t)nnz * 4);
   P.off.var_ell = put((size_t)kEll * n * 4);
+  P.off.wide_vars = put(P.wide_vars.size() * 4);
   P.off.c = put((size_t)n * 8);
   P.off.invdeg = put((size_t)n * 4);
   P.off.inst_row_ptr = put((size_t)(ni + 1) * 8);
@@ -793,6 +796,7 @@ dg_status validate_plan(const Plan& P) {
   // variables: CSR and ELL columns point back at their own slots, rows ascending
   if ((int64_t)P.var_ptr.size() != (int64_t)n + 1 || P.var_ptr[0] != 0 || P.var_ptr[n] != NL)
     return bad("variable pointers malformed");
+  size_t next_wide = 0;
   for (int32_t i = 0; i < n; ++i) {
     if (P.var_ptr[i + 1] < P.var_ptr[i]) return bad("variable pointers not monotone");
     int prev_row = -1;
@@ -812,7 +816,13 @@ dg_status validate_plan(const Plan& P) {
       const int32_t want = r < d ? P.var_slots[P.var_ptr[i] + r] : -1;
       if (e != want) return bad("variable " + std::to_string(i) + ": ELL column disagrees with the slot list");
     }
+    if (d > kWide) {
+      if (next_wide >= P.wide_vars.size() || P.wide_vars[next_wide] != i)
+        return bad("variable " + std::to_string(i) + ": missing from the wide-variable list");
+      ++next_wide;
+    }
   }
+  if (next_wide != P.wide_vars.size()) return bad("wide-variable list lists a narrow variable");
   // launch groups cover the tiles in order
   int32_t t0 = 0;
   for (const LaunchGroup& g : P.groups) {

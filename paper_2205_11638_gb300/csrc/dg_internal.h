@@ -28,6 +28,9 @@ constexpr int kStreams = 4;    // streams one sweep's launch groups run on
 // than kEll slots stores its last ELL entry as -2 - slot, the rest coming
 // from var_slots[var_ptr[i] + kEll ..].
 constexpr int kEll = 4;
+// Variables with more slots than this ("wide") are reduced by a warp each in
+// the per-variable kernels, listed in wide_vars; the others by a thread each.
+constexpr int kWide = 32;
 
 // One tile = up to 32 BDDs swept by one warp, BDD b by lane b.  Per-tile
 // arrays are interleaved by lane: slot (h, b) is slot_base + 32 h + b (its
@@ -81,6 +84,8 @@ struct DevArena {
   const int32_t* var_ptr;   // CSR over variables: slots of variable i
   const int32_t* var_slots; // arena slots, grouped by variable, rows ascending
   const int32_t* var_ell;   // [kEll * n] the first kEll slots of each variable (see kEll)
+  const int32_t* wide_vars; // the variables with more than kWide slots, ascending
+  int32_t num_wide;
   const double* c;          // objective, float64[n]
   const float* invdeg;      // 1/|J_i| (0 for uncovered variables)
   const int64_t* inst_row_ptr;
@@ -153,7 +158,7 @@ struct Plan {
   std::vector<uint16_t> desc;
   std::vector<uint16_t> lohi8;
   std::vector<int32_t> slot_var, slot_row;
-  std::vector<int32_t> var_ptr, var_slots, var_ell;
+  std::vector<int32_t> var_ptr, var_slots, var_ell, wide_vars;
   std::vector<double> c;
   std::vector<float> invdeg;
   std::vector<int64_t> inst_row_ptr;
@@ -178,7 +183,8 @@ struct Plan {
   int32_t long_slot_base = 0, long_cost_size = 0, long_stream = 0;
   // byte offsets of every array inside the arena
   struct Off {
-    size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, c, invdeg, inst_row_ptr, inst_var_ptr,
+    size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, wide_vars, c, invdeg, inst_row_ptr,
+        inst_var_ptr,
         lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, S, Sbar, slot_avg, E, lb_part,
         long_d, long_t, nodecost, total;
   } off{};

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
     if (more) {
       b = __ldg(A.var_ptr + i) + kEll;
       e = __ldg(A.var_ptr + i + 1);
+      if (e - b > kWide - kEll) return;  // a wide variable: k_reduce_wide's
       for (int k = b; k < e; ++k) s += M[__ldg(A.var_slots + k)];
     }
     const float sbar = __ldg(A.invdeg + i) * s;
@@ -75,6 +76,34 @@ __global__ void __launch_bounds__(256) k_reduce_S(DevArena A, const float* __res
       lam[q] = (float)((double)lam[q] + w * r);
       if (SCATTER) A.slot_avg[q] = t;
     }
+  }
+}
+
+// k_reduce_S<false, SCATTER> for the wide variables (more than kWide slots),
+// one warp each: the lanes load 32 of the variable's M values at a time and
+// every lane adds them in slot order (the plain loop's order, so S is the
+// same to the bit); lane 0 stores S.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_reduce_wide(DevArena A, const float* __restrict__ M, int mode) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (w >= A.num_wide) return;  // the whole warp
+  const int i = __ldg(A.wide_vars + w);
+  const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
+  float s = 0.f;
+  for (int c = b; c < e; c += 32) {
+    const float v = c + lane < e ? M[__ldg(A.var_slots + c + lane)] : 0.f;
+    const int cnt = min(32, e - c);
+    for (int j = 0; j < cnt; ++j) s += __shfl_sync(kAll, v, j);
+  }
+  const float sbar = __ldg(A.invdeg + i) * s;
+  if (lane == 0) {
+    A.S[i] = s;
+    A.Sbar[i] = sbar;
+  }
+  if (SCATTER) {
+    const float t = mode == 1 ? s : sbar;
+    for (int k = b + lane; k < e; k += 32) A.slot_avg[__ldg(A.var_slots + k)] = t;
   }
 }
 
@@ -179,6 +208,7 @@ __global__ void __launch_bounds__(256) k_slot_inputs(DevArena A, const float* __
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
+  if (e - b > kWide) return;  // a wide variable: k_slot_inputs_wide's
   float s = 0.f;
   if (x)
     for (int k = b; k < e; ++k) s += x[__ldg(A.var_slots + k)];
@@ -188,6 +218,33 @@ __global__ void __launch_bounds__(256) k_slot_inputs(DevArena A, const float* __
   if (slot_in) {
     const float4 t = make_float4(s, S_var ? S_var[i] : 0.f, __ldg(A.invdeg + i), 0.f);
     for (int k = b; k < e; ++k) slot_in[__ldg(A.var_slots + k)] = t;
+  }
+}
+
+// k_slot_inputs for the wide variables, one warp each (the sum in slot order
+// as in k_reduce_wide).
+__global__ void __launch_bounds__(256) k_slot_inputs_wide(DevArena A, const float* __restrict__ x,
+                                                           const float* __restrict__ sd_in, float* out_var,
+                                                           const float* __restrict__ S_var, float4* slot_in) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (w >= A.num_wide) return;  // the whole warp
+  const int i = __ldg(A.wide_vars + w);
+  const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
+  float s = 0.f;
+  if (x) {
+    for (int c = b; c < e; c += 32) {
+      const float v = c + lane < e ? x[__ldg(A.var_slots + c + lane)] : 0.f;
+      const int cnt = min(32, e - c);
+      for (int j = 0; j < cnt; ++j) s += __shfl_sync(kAll, v, j);
+    }
+  } else if (sd_in) {
+    s = sd_in[i];
+  }
+  if (out_var && lane == 0) out_var[i] = s;
+  if (slot_in) {
+    const float4 t = make_float4(s, S_var ? S_var[i] : 0.f, __ldg(A.invdeg + i), 0.f);
+    for (int k = b + lane; k < e; k += 32) slot_in[__ldg(A.var_slots + k)] = t;
   }
 }
 
@@ -203,6 +260,8 @@ void launch_slot_inputs(const DevArena& A, const float* x, const float* sd_in, f
   const int T = 256;
   const int G = (A.n + T - 1) / T;
   if (G > 0) k_slot_inputs<<<G, T, 0, st>>>(A, x, sd_in, out_var, S_var, slot_in);
+  if (A.num_wide > 0)
+    k_slot_inputs_wide<<<(A.num_wide + 7) / 8, 256, 0, st>>>(A, x, sd_in, out_var, S_var, slot_in);
 }
 
 void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st) {
@@ -219,9 +278,13 @@ void launch_reduce_S(const DevArena& A, const float* M, float* lam, const float*
   if (renorm)
     for_sweep ? k_reduce_S<true, true><<<G, T, 0, st>>>(A, M, lam, alpha, mode)
               : k_reduce_S<true, false><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
-  else
+  else {
     for_sweep ? k_reduce_S<false, true><<<G, T, 0, st>>>(A, M, lam, alpha, mode)
               : k_reduce_S<false, false><<<G, T, 0, st>>>(A, M, lam, alpha, mode);
+    if (A.num_wide > 0)
+      for_sweep ? k_reduce_wide<true><<<(A.num_wide + 7) / 8, 256, 0, st>>>(A, M, mode)
+                : k_reduce_wide<false><<<(A.num_wide + 7) / 8, 256, 0, st>>>(A, M, mode);
+  }
 }
 
 void launch_init(const DevArena& A, float* lam, float* M, cudaStream_t st) {
