@@ -827,6 +827,12 @@ dg_status enqueue_recorded_segment(dg_arena* ar, cudaStream_t st, float* lam, fl
     ra.rec_diff = (float*)(w + L.rec_diff) + (size_t)sw * NS;
     ra.rec_lmeta = (int32_t*)(w + L.rec_lmeta + (size_t)sw * L.lmeta_stride);
     ra.rec_lamin = (int2*)(w + L.rec_lamin + (size_t)sw * L.lamin_stride);
+    // each recording sweep hands its path costs (and records) to the next
+    ra.cost_out = A.nodecost;
+    if (sw > 0) {
+      ra.cost_in = A.nodecost;
+      ra.meta_in = (const uint16_t*)(w + L.rec_meta + (size_t)(sw - 1) * L.meta_stride);
+    }
     if (lb_out && sw == 2 * k - 1) ra.E = A.E;
     launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads_of(opts), ar->groups.data(), (int)ar->groups.size(),
                  streams_for(ar, st));
@@ -978,6 +984,11 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       ra.rec_diff = rec_diff + (size_t)sw * NS;
       ra.rec_lmeta = (int32_t*)(w + L.rec_lmeta + (size_t)sw * L.lmeta_stride);
       ra.rec_lamin = (int2*)(w + L.rec_lamin + (size_t)sw * L.lamin_stride);
+      ra.cost_out = A.nodecost;  // handed on from recording sweep to recording sweep
+      if (sw > 0) {
+        ra.cost_in = A.nodecost;
+        ra.meta_in = (const uint16_t*)(rec_meta + (size_t)(sw - 1) * L.meta_stride);
+      }
       launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads, ar->groups.data(), (int)ar->groups.size(),
                    streams_for(ar, st));
     }

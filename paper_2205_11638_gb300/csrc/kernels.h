@@ -20,9 +20,9 @@ struct SweepArgs {
   float omega0;        // mode 0
   int mode;
   float* E;            // nullable: E^j per original row (kBwd, kEnergy)
-  // Hand-off of App. B's path costs from one plain sweep to the next (per
-  // node and lane of the tiles, in the layout of the child codes; both
-  // nullable; kFwd / kBwd only).  cost_out: the costs of the sweep's own
+  // Hand-off of App. B's path costs from one update sweep (plain or
+  // recording) to the next (per node and lane of the tiles, in the layout of
+  // the child codes; both nullable).  cost_out: the costs of the sweep's own
   // direction under the outgoing lambda, which it computes anyway (SP(r, .)
   // after a forward sweep, SP(., T) after a backward one).  cost_in: the
   // costs opposite to the sweep direction under the incoming lambda (SP(., T)
@@ -32,6 +32,9 @@ struct SweepArgs {
   // before it writes it.
   float* cost_out;
   const float* cost_in;
+  // kFwdRec / kBwdRec with cost_in: the node records (rec_meta) of the
+  // recording sweep that wrote the costs
+  const uint16_t* meta_in;
   // argmin records (kFwdRec, kBwdRec), read back by the adjoint of the sweep:
   uint16_t* rec_meta;  // per node (layout of the child codes): in-arc parent | beta << 8 | hi-choice << 9
   uint16_t* rec_amin;  // per slot: argmin node of m0 | argmin node of m1 << 8

@@ -41,16 +41,29 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
   const Tile T = A.tiles[tile];
   TileSmem s = carve<MODE, !BWD, REC>(smem + (size_t)warp * region_bytes, T);
   // a plain sweep may take the opposite-direction costs from the sweep before it
-  const float* cost_in = (KIND == kFwd || KIND == kBwd) ? a.cost_in : nullptr;
+  const float* cost_in = (FWD || BWD) ? a.cost_in : nullptr;
   load_tile<FWD || BWD, MODE>(A, T, s, a.lam, a.omega, a.alpha, lane, cost_in);
+  // a recording sweep that takes the costs also takes the records the
+  // recording sweep before it made in the same comparisons: the out-arc
+  // choices of SP(., T) (for a forward sweep) or the in-arcs of SP(r, .)
+  // (for a backward one); the rest of each record is rewritten below
+  if (REC && cost_in) {
+    copy_async(s.meta + 2 * kWarp, a.meta_in + T.node_base, (s.nmax - 2) * kWarp * 2, lane);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+    if (FWD && desc_width(s.desc[lane]) > 0) DG_META(s, 2) &= kHiChoice;  // the root has no in-arc
+  }
   const int64_t sbase = T.slot_base;
 
   if (FWD || KIND == kMinMarg) {
     // ---- SP(., T) under lambda at sweep start, then the forward sweep -----
-    if (REC)
-      lane_cost_to_top_rec(s, lane);
-    else if (!cost_in)
-      lane_cost_to_top(s, lane);
+    if (!cost_in) {
+      if (REC)
+        lane_cost_to_top_rec(s, lane);
+      else
+        lane_cost_to_top(s, lane);
+    }
     if (desc_width(s.desc[lane]) > 0) DG_R(s, 2) = 0.0f;
     for (int h = 0; h < s.nh; ++h) {
       const uint32_t ds = s.desc[h * kWarp + lane];
@@ -73,7 +86,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         if (i < w) {
           cc[i] = node_code(s, fn + i, lane);
           dd[i] = DG_R(s, fn + i);
-          if (KIND == kFwd) DG_F(s, fn + i) = dd[i];
+          if (FWD) DG_F(s, fn + i) = dd[i];
           b0 = fminf(b0, dd[i] + DG_F(s, cc[i] & 0xFFu));
           b1 = fminf(b1, dd[i] + DG_F(s, cc[i] >> 8));
         }
@@ -86,7 +99,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         const float x0 = dv + DG_F(s, c & 0xFFu), x1 = dv + DG_F(s, c >> 8);
         // SP(r, n) is final here and SP(n, T) is not read again: the whole
         // array ends the sweep holding SP(r, .) under the new lambda
-        if (KIND == kFwd) DG_F(s, n) = dv;
+        if (FWD) DG_F(s, n) = dv;
         if (REC) {
           if (x0 < b0) { b0 = x0; v0 = n; }
           if (x1 < b1) { b1 = x1; v1 = n; }
@@ -146,13 +159,15 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
         }
       }
     }
-    if (KIND == kFwd && a.cost_out) store_costs(a.cost_out + T.node_base, s.full, s.nmax, lane);
+    if (FWD && a.cost_out) store_costs(a.cost_out + T.node_base, s.full, s.nmax, lane);
   } else if (BWD) {
     // ---- SP(r, .) under lambda at sweep start, then the backward sweep ----
-    if (REC)
-      lane_cost_from_root_rec(s, lane);
-    else if (!cost_in)
-      lane_cost_from_root(s, lane);
+    if (!cost_in) {
+      if (REC)
+        lane_cost_from_root_rec(s, lane);
+      else
+        lane_cost_from_root(s, lane);
+    }
     DG_W(s, kTopCode) = 0.0f;
     DG_W(s, kBotCode) = f_inf();
     for (int h = s.nh - 1; h >= 0; --h) {
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(128) k_sweep(DevArena A, SweepArgs a, int regi
       }
     }
     // the second whole array ends the sweep holding SP(., T) under the new lambda
-    if (KIND == kBwd && a.cost_out) store_costs(a.cost_out + T.node_base, s.ring, s.nmax, lane);
+    if (BWD && a.cost_out) store_costs(a.cost_out + T.node_base, s.ring, s.nmax, lane);
   } else {
     // kEnergy / kSeed: SP(., T) under lambda
     lane_cost_to_top(s, lane);
