@@ -37,6 +37,37 @@ def test_noalloc_bound_matches_lower_bound_twice(make):
         assert np.all(np.abs(g - w) <= 1e-5 * np.maximum(1.0, np.abs(w))), (call, g, w)
 
 
+def test_noalloc_bound_captured_in_a_cuda_graph():
+    # the reason for the entry point: a bound inside a stream capture (after a
+    # first eager call has looked up the static array), replayed later
+    build.build()
+    lib = _lib.load()
+    prob = workloads.matching_quadratic(L=60, R=60, pairs=2500, seed=12)
+    A = solver.plan(prob).bind()
+    lam, M = A.init_lambda()
+    A.iterate(lam, M, iters=2)
+    out = torch.zeros(A.num_inst, dtype=torch.float64, device=A.device)
+    args = [ctypes.c_void_p(t.data_ptr()) for t in (lam, M, out)]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        st = lib.dg_lower_bound_noalloc(A._h, ctypes.c_void_p(side.cuda_stream), *args)  # eager first call
+        assert st == _lib.DG_OK, lib.dg_last_error()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            st = lib.dg_lower_bound_noalloc(A._h, ctypes.c_void_p(side.cuda_stream), *args)
+        assert st == _lib.DG_OK, lib.dg_last_error()
+    torch.cuda.current_stream().wait_stream(side)
+    for k in range(2):
+        A.iterate(lam, M, iters=1)   # new state; the graph reads the same buffers
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        want = A.lower_bound(lam, M).cpu().numpy()
+        got = out.cpu().numpy()
+        assert np.all(np.abs(got - want) <= 1e-5 * np.maximum(1.0, np.abs(want))), (k, got, want)
+
+
 def test_noalloc_rejects_arena_beyond_static_limit():
     build.build()
     lib = _lib.load()
