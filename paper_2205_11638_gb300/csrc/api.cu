@@ -832,6 +832,7 @@ dg_status enqueue_recorded_segment(dg_arena* ar, cudaStream_t st, float* lam, fl
     if (sw > 0) {
       ra.cost_in = A.nodecost;
       ra.meta_in = (const uint16_t*)(w + L.rec_meta + (size_t)(sw - 1) * L.meta_stride);
+      ra.lmeta_in = (const int32_t*)(w + L.rec_lmeta + (size_t)(sw - 1) * L.lmeta_stride);
     }
     if (lb_out && sw == 2 * k - 1) ra.E = A.E;
     launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads_of(opts), ar->groups.data(), (int)ar->groups.size(),
@@ -988,6 +989,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
       if (sw > 0) {
         ra.cost_in = A.nodecost;
         ra.meta_in = (const uint16_t*)(rec_meta + (size_t)(sw - 1) * L.meta_stride);
+        ra.lmeta_in = (const int32_t*)(w + L.rec_lmeta + (size_t)(sw - 1) * L.lmeta_stride);
       }
       launch_sweep(sw % 2 == 0 ? kFwdRec : kBwdRec, A, ra, threads, ar->groups.data(), (int)ar->groups.size(),
                    streams_for(ar, st));

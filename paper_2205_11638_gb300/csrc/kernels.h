@@ -32,9 +32,10 @@ struct SweepArgs {
   // before it writes it.
   float* cost_out;
   const float* cost_in;
-  // kFwdRec / kBwdRec with cost_in: the node records (rec_meta) of the
-  // recording sweep that wrote the costs
+  // kFwdRec / kBwdRec with cost_in: the node records (rec_meta, and
+  // rec_lmeta for the long BDDs) of the recording sweep that wrote the costs
   const uint16_t* meta_in;
+  const int32_t* lmeta_in;
   // argmin records (kFwdRec, kBwdRec), read back by the adjoint of the sweep:
   uint16_t* rec_meta;  // per node (layout of the child codes): in-arc parent | beta << 8 | hi-choice << 9
   uint16_t* rec_amin;  // per slot: argmin node of m0 | argmin node of m1 << 8

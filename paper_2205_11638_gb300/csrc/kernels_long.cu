@@ -14,6 +14,9 @@
 // children, so no two lanes write the same node and nothing needs atomics.
 // Path costs live in the arena's scratch (long_d, long_t, indexed by node
 // number: 0 top, 1 bottom, own nodes from 2), read and written through L1.
+// A sweep leaves there the costs of its own direction under the new lambda,
+// so a sweep handed the costs (SweepArgs::cost_in, set when the tiles' costs
+// are handed on) skips its first pass: they are already in place.
 //
 // The arithmetic is the lane kernels': the same FP32 operations per arc;
 // minima are exact, so values do not depend on the order of the reduction;
@@ -97,11 +100,22 @@ __device__ __forceinline__ LongCtx long_ctx(const DevArena& A, int b) {
   return c;
 }
 
-// alpha_ij S_i of slot q (mode 1), S_i / |J_i| (mode 0)
+// alpha_ij S_i of slot q (mode 1), S_i / |J_i| (mode 0), from the per-slot
+// terms the S reduction before the sweep wrote
 template <int MODE>
 __device__ __forceinline__ float long_avg(const DevArena& A, const SweepArgs& a, int64_t q) {
-  const int v = __ldg(A.slot_var + q);
-  return MODE == 1 ? a.alpha[q] * A.S[v] : A.Sbar[v];
+  return MODE == 1 ? a.alpha[q] * A.slot_avg[q] : A.slot_avg[q];
+}
+
+// The records of a recording sweep handed the costs: the choices the
+// recording sweep before it made in the same comparisons (keep: kLHi, the
+// out-arc choices of SP(., T), for a forward sweep; the in-arcs of SP(r, .)
+// for a backward one), the rest cleared for the sweep to write.
+__device__ __forceinline__ void long_take_records(const LongCtx& c, const int32_t* prev, int32_t* meta, int32_t keep,
+                                                  int lane) {
+  const int e = c.lvl[c.B.k];
+  for (int n = 2 + lane; n < e; n += kWarp) meta[n] = prev[n] & keep;
+  __syncwarp();
 }
 
 // SP(., T) of every node under lam, levels bottom-up.  REC: the record of
@@ -225,9 +239,13 @@ __global__ void __launch_bounds__(128) k_long_sweep(DevArena A, SweepArgs a) {
   const int64_t sb = c.B.slot_base;
   const int k = c.B.k;
   int32_t* meta = REC ? a.rec_lmeta + c.B.cost_base : nullptr;
+  const bool handed = (FWD || BWD) && a.cost_in != nullptr;
 
   if (FWD || KIND == kMinMarg) {
-    long_cost_to_top<REC>(c, a.lam, meta, lane);
+    if (!handed)
+      long_cost_to_top<REC>(c, a.lam, meta, lane);
+    else if (REC)
+      long_take_records(c, a.lmeta_in + c.B.cost_base, meta, kLHi, lane);
     if (lane == 0) c.d[2] = 0.0f;
     __syncwarp();
     for (int h = 0; h < k; ++h) {
@@ -263,7 +281,10 @@ __global__ void __launch_bounds__(128) k_long_sweep(DevArena A, SweepArgs a) {
       __syncwarp();
     }
   } else if (BWD) {
-    long_cost_from_root<REC>(c, a.lam, meta, lane);
+    if (!handed)
+      long_cost_from_root<REC>(c, a.lam, meta, lane);
+    else if (REC)
+      long_take_records(c, a.lmeta_in + c.B.cost_base, meta, ~kLHi, lane);
     if (lane == 0) {
       c.t[kTopCode] = 0.0f;
       c.t[kBotCode] = f_inf();
