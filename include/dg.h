@@ -121,8 +121,9 @@ typedef struct dg_stats {
   double bytes_per_iter;        /* algorithmic bytes of one plain iteration:
                                    32*N_v + 48*N_lambda + 16*n */
   double actual_bytes_per_iter; /* bytes the kernels of this layout move per
-                                   plain iteration (16-bit child indices,
-                                   recomputed path costs) */
+                                   plain iteration (8-bit child codes, path
+                                   costs handed from sweep to sweep, per-slot
+                                   averaging terms) */
   int64_t hop_histogram[64];    /* BDDs by hop count (last bin: >= 63) */
 } dg_stats;
 

@@ -395,14 +395,15 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   const double Nv = (double)P.sizes.num_nodes, Nl = (double)P.sizes.num_lambda, n = (double)P.sizes.n;
   S.bytes_per_iter = 32.0 * Nv + 48.0 * Nl + 16.0 * n;
   const double NVp = (double)P.sizes.num_nodes_padded, ns = (double)P.sizes.num_slots;
-  // per sweep: children 2 B per node; descriptor, variable, lambda read and
-  // write, M write 20 B per slot; alpha and S gathers 8 B per lambda.  Per
-  // S reduction: variable CSR and M gather 8 B per lambda, pointers and S 8 B
-  // per variable.
-  // long BDDs per sweep: children 8 B and in-arcs ~8 B per node, both path
-  // costs read and written 16 B per node
-  S.actual_bytes_per_iter = 2.0 * (2.0 * NVp + 20.0 * ns + 8.0 * Nl) + 2.0 * (8.0 * n + 8.0 * Nl) +
-                            2.0 * 32.0 * (double)P.sizes.num_long_nodes;
+  // per sweep (the path costs handed on, as inside dg_iterate): children
+  // 2 B and the costs read and written 8 B per node; descriptor, lambda read
+  // and write, M write, averaging term 18 B per slot; alpha 4 B per lambda
+  // (mode 1).  Per S reduction: M read and averaging term written 8 B per
+  // lambda, ELL columns 16 B and S, S/|J_i| 8 B per variable.
+  // long BDDs per sweep: children 8 B, in-arcs ~8 B and the path costs 8 B
+  // per node
+  S.actual_bytes_per_iter = 2.0 * (10.0 * NVp + 18.0 * ns + 4.0 * Nl) + 2.0 * (24.0 * n + 8.0 * Nl) +
+                            2.0 * 24.0 * (double)P.sizes.num_long_nodes;
   for (int i = 0; i < 64; ++i) S.hop_histogram[i] = P.hop_histogram[i];
   *out = ar;
   return DG_OK;

@@ -197,7 +197,7 @@ struct Plan {
 // kernels: the costs of the first pass (32 x nmax floats), a ring of two
 // levels for the costs of the sweep direction (32 x ring floats), the child
 // codes of 32 x (nmax - 2) nodes, and per slot its descriptor, lambda, the
-// gathered S term and (mode 1) omega and alpha.
+// averaging term and (mode 1) omega and alpha.
 inline size_t sweep_smem_bytes(int nmax, int nhops, int mode, int ring) {
   size_t b = (size_t)nmax * kWarp * 4 + (size_t)ring * kWarp * 4 + (size_t)(nmax - 2) * kWarp * 2 +
              (size_t)nhops * kWarp * (mode ? 18 : 10);
