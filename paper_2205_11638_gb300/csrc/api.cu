@@ -366,6 +366,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.long_d = (float*)(b + P.off.long_d);
   A.long_t = (float*)(b + P.off.long_t);
   A.nodecost = (float*)(b + P.off.nodecost);
+  A.slot_invdeg = (float*)(b + P.off.slot_invdeg);
   A.S = (float*)(b + P.off.S);
   A.Sbar = (float*)(b + P.off.Sbar);
   A.slot_avg = (float*)(b + P.off.slot_avg);
@@ -381,6 +382,14 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.long_slot_base = P.long_slot_base;
   A.long_cost_size = P.long_cost_size;
   A.long_stream = P.long_stream;
+  // the per-slot weights of mode 0 the adjoint reads, laid out once
+  launch_fill_slot_invdeg(A, st);
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    dg_destroy(ar);
+    return cuda_fail(e, "dg_bind: per-slot weights");
+  }
   ar->sizes = P.sizes;
   ar->smem_sweep = P.smem_sweep;
   ar->groups = P.groups;
@@ -784,7 +793,7 @@ BwdLayout backward_layout(const dg_arena* ar, int iters, int ckpt_every) {
   L.sdot = put(NS * 4);
   L.sd_a = put(n * 4);
   L.sd_b = put(n * 4);
-  L.slot_in = put(NS * 16);  // float4 per slot: the adjoint sweep's per-variable inputs
+  L.slot_in = put(NS * 8);  // float2 per slot: the adjoint sweep's per-variable inputs
   // long BDDs: node and slot records of every sweep of one segment, and the
   // per-node gradients of the adjoint
   const size_t lcost = (size_t)ar->dev.long_cost_size, lslots = NS - (size_t)ar->dev.long_slot_base;
@@ -910,7 +919,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   float* sdot = (float*)(w + L.sdot);
   float* sd_next = (float*)(w + L.sd_a);
   float* sd_cur = (float*)(w + L.sd_b);
-  float4* slot_in = (float4*)(w + L.slot_in);
+  float2* slot_in = (float2*)(w + L.slot_in);
   const int threads = threads_of(opts);
   SweepArgs fa{};
   fa.lam = w_lam;
@@ -965,7 +974,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   aa.sdot = sdot;
   aa.slot_in = slot_in;
   // padding slots belong to no variable: their inputs stay 0
-  if (e == cudaSuccess && iters > 0) e = cudaMemsetAsync(slot_in, 0, NS * 16, st);
+  if (e == cudaSuccess && iters > 0) e = cudaMemsetAsync(slot_in, 0, NS * 8, st);
   aa.long_a1 = (float*)(w + L.long_a1);
   aa.long_a2 = (float*)(w + L.long_a2);
   const int last_sweep = 2 * iters - 1;

@@ -630,6 +630,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.long_d = put((size_t)P.long_cost_size * 4);
   P.off.long_t = put((size_t)P.long_cost_size * 4);
   P.off.nodecost = put(P.lohi8.size() * 4);
+  P.off.slot_invdeg = put((size_t)num_slots * 4);
   P.off.total = o;
   P.smem_sweep = align_up(smem_max, 16);
   P.smem_adjoint = align_up(smem_adj_max, 16);

@@ -104,6 +104,9 @@ struct DevArena {
   // scratch per node and lane of the tiles (layout of lohi8): SP(r, .) as a
   // forward sweep leaves it for the backward sweep after it (see SweepArgs)
   float* nodecost;
+  // per slot: 1/|J_i| of its variable (0 for padding), filled when the arena
+  // is bound; the adjoint's alpha in mode 0
+  float* slot_invdeg;
   float* S;                 // scratch: per-variable sum of M (snapshot)
   float* Sbar;              // scratch: S_i / |J_i| (the mode-0 averaging term)
   float* slot_avg;          // scratch per slot: the averaging term of its variable (Sbar_i in mode 0,
@@ -186,7 +189,7 @@ struct Plan {
     size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, wide_vars, c, invdeg, inst_row_ptr,
         inst_var_ptr,
         lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, S, Sbar, slot_avg, E, lb_part,
-        long_d, long_t, nodecost, total;
+        long_d, long_t, nodecost, slot_invdeg, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels
   size_t smem_adjoint = 0; // dynamic smem of the adjoint kernels

@@ -95,11 +95,11 @@ struct AdjArgs {
   int mode;
   const float* seed_M;     // nullable: gradient of the sweep's M output (per slot)
   const float* sdot_next;  // nullable: S-dot of the next sweep (per variable)
-  // per slot: {S-dot of the next sweep, S at the sweep's start, 1/|J_i|, 0}
-  // of the slot's variable (launch_slot_inputs), what the tiles' reverse
-  // reads instead of gathering per variable; the long BDDs use the
-  // per-variable arrays above
-  const float4* slot_in;
+  // per slot: {S-dot of the next sweep, S at the sweep's start} of the
+  // slot's variable (launch_slot_inputs), what the tiles' reverse reads
+  // instead of gathering per variable (with DevArena::slot_invdeg for the
+  // weights of mode 0); the long BDDs use the per-variable arrays above
+  const float2* slot_in;
   float* g_lam;            // in: gradient of lambda after the sweep; out: before
   float* g_omega;          // accumulated
   float* g_alpha;          // accumulated
@@ -116,10 +116,12 @@ void launch_adjoint_sweep(bool forward, const DevArena& A, const AdjArgs& a, con
                           size_t cta_smem_cap, const StreamSet& ss);
 // Per variable i: s_i = sum over the slots q of i of x[q] (fixed order), or
 // sd_in[i] when x is NULL (0 when both are); out_var[i] = s_i (nullable);
-// and, when slot_in is not NULL, slot_in[q] = {s_i, S_var[i] (0 if NULL),
-// 1/|J_i|, 0} for every slot q of i.
+// and, when slot_in is not NULL, slot_in[q] = {s_i, S_var[i] (0 if NULL)}
+// for every slot q of i.
 void launch_slot_inputs(const DevArena& A, const float* x, const float* sd_in, float* out_var, const float* S_var,
-                        float4* slot_in, cudaStream_t st);
+                        float2* slot_in, cudaStream_t st);
+// A.slot_invdeg[q] = 1/|J_i| of the variable of slot q (0 for padding)
+void launch_fill_slot_invdeg(const DevArena& A, cudaStream_t st);
 // out_slot[q] = v[variable of q] (0 for padding slots)
 void launch_gather_var(const DevArena& A, const float* v, float* out_slot, cudaStream_t st);
 

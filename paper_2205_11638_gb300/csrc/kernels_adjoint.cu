@@ -76,11 +76,11 @@ __device__ __forceinline__ LevelIn load_level(const DevArena& A, const AdjArgs& 
                                               int h, int lane) {
   LevelIn r;
   const int q = h * kWarp + lane;
-  const float4 in = a.slot_in[sb + q];
+  const float2 in = a.slot_in[sb + q];
   r.diff = a.rec_diff[sb + q];
   r.amin = a.rec_amin[sb + q];
   r.S = in.y;
-  r.al = MODE == 1 ? a.alpha[sb + q] : in.z;
+  r.al = MODE == 1 ? a.alpha[sb + q] : A.slot_invdeg[sb + q];
   r.om = MODE == 1 ? a.omega[sb + q] : a.omega0;
   const float seed = a.seed_M ? a.seed_M[sb + q] : 0.0f;
   r.md = seed + in.x;  // gradient of M^new

@@ -204,7 +204,7 @@ __global__ void k_seed_M(DevArena A, float* gM) {
 // contributions) and the per-slot inputs of the next adjoint sweep.
 __global__ void __launch_bounds__(256) k_slot_inputs(DevArena A, const float* __restrict__ x,
                                                       const float* __restrict__ sd_in, float* out_var,
-                                                      const float* __restrict__ S_var, float4* slot_in) {
+                                                      const float* __restrict__ S_var, float2* slot_in) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const int b = __ldg(A.var_ptr + i), e = __ldg(A.var_ptr + i + 1);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_slot_inputs(DevArena A, const float* __
     s = sd_in[i];
   if (out_var) out_var[i] = s;
   if (slot_in) {
-    const float4 t = make_float4(s, S_var ? S_var[i] : 0.f, __ldg(A.invdeg + i), 0.f);
+    const float2 t = make_float2(s, S_var ? S_var[i] : 0.f);
     for (int k = b; k < e; ++k) slot_in[__ldg(A.var_slots + k)] = t;
   }
 }
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_slot_inputs(DevArena A, const float* __
 // as in k_reduce_wide).
 __global__ void __launch_bounds__(256) k_slot_inputs_wide(DevArena A, const float* __restrict__ x,
                                                            const float* __restrict__ sd_in, float* out_var,
-                                                           const float* __restrict__ S_var, float4* slot_in) {
+                                                           const float* __restrict__ S_var, float2* slot_in) {
   constexpr unsigned kAll = 0xffffffffu;
   const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (w >= A.num_wide) return;  // the whole warp
@@ -243,9 +243,22 @@ __global__ void __launch_bounds__(256) k_slot_inputs_wide(DevArena A, const floa
   }
   if (out_var && lane == 0) out_var[i] = s;
   if (slot_in) {
-    const float4 t = make_float4(s, S_var ? S_var[i] : 0.f, __ldg(A.invdeg + i), 0.f);
+    const float2 t = make_float2(s, S_var ? S_var[i] : 0.f);
     for (int k = b + lane; k < e; k += 32) slot_in[__ldg(A.var_slots + k)] = t;
   }
+}
+
+__global__ void k_slot_invdeg(DevArena A) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.num_slots) return;
+  const int var = __ldg(A.slot_var + q);
+  A.slot_invdeg[q] = var >= 0 ? __ldg(A.invdeg + var) : 0.f;
+}
+
+void launch_fill_slot_invdeg(const DevArena& A, cudaStream_t st) {
+  const int T = 256;
+  const int64_t G = (A.num_slots + T - 1) / T;
+  if (G > 0) k_slot_invdeg<<<(unsigned)G, T, 0, st>>>(A);
 }
 
 __global__ void k_gather_var(DevArena A, const float* __restrict__ v, float* out) {
@@ -256,7 +269,7 @@ __global__ void k_gather_var(DevArena A, const float* __restrict__ v, float* out
 }
 
 void launch_slot_inputs(const DevArena& A, const float* x, const float* sd_in, float* out_var, const float* S_var,
-                        float4* slot_in, cudaStream_t st) {
+                        float2* slot_in, cudaStream_t st) {
   const int T = 256;
   const int G = (A.n + T - 1) / T;
   if (G > 0) k_slot_inputs<<<G, T, 0, st>>>(A, x, sd_in, out_var, S_var, slot_in);
