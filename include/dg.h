@@ -364,7 +364,10 @@ dg_status dg_smoothed_dual(dg_arena* arena, void* stream, const float* lam, floa
 /* --- CUDA graph of the iteration loop ------------------------------------ */
 
 /* Captures `iters` iterations of dg_iterate (same arguments) into a CUDA
- * graph; dg_graph_replay launches it on stream.  Pointers are baked in. */
+ * graph; dg_graph_replay launches it on stream.  Pointers are baked in, the
+ * arena's among them: the graph must not outlive the arena, and a replay
+ * counts as a call on the arena (no path-cost hand-off across it; the
+ * arena's averaging terms are then those of the graph's mode). */
 dg_status dg_graph_create(dg_arena* arena, void* stream, float* lam, float* M, const float* omega, const float* alpha,
                           int32_t mode, int32_t iters, double* lb_out, const dg_options* opts, dg_graph_t** out);
 dg_status dg_graph_replay(dg_graph_t* g, void* stream);

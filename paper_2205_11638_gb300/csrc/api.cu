@@ -53,6 +53,10 @@ struct dg_arena_s {
 struct dg_graph_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // the arena the graph iterates, and its mode: a replay rewrites the
+  // arena's per-slot averaging terms and handed-on path costs
+  dg_arena* arena = nullptr;
+  int mode = 0;
 };
 
 namespace {
@@ -740,12 +744,19 @@ dg_status dg_graph_create(dg_arena* ar, void* stream, float* lam, float* M, cons
   dg_graph_t* G = new dg_graph_t();
   G->graph = g;
   G->exec = x;
+  G->arena = ar;
+  G->mode = mode;
   *out = G;
   return DG_OK;
 }
 
 dg_status dg_graph_replay(dg_graph_t* g, void* stream) {
   if (!g) return fail(DG_EINVAL, "dg_graph_replay: null graph");
+  if (g->arena) {
+    // no hand-off across the replay; the per-slot terms are now the graph's
+    ++g->arena->epoch;
+    g->arena->avg_mode = g->mode;
+  }
   cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "dg_graph_replay");
   return DG_OK;

@@ -169,3 +169,29 @@ def test_sweep_mode_must_match_the_last_reduction():
     A.sum_M(M, alpha=al)                        # mode 1
     A.sweep(lam, M, forward=True, omega=om, alpha=al)
     torch.cuda.synchronize()
+
+
+def test_graph_replay_counts_as_a_call_on_the_arena():
+    prob = workloads.matching_quadratic(L=30, R=30, pairs=800, seed=39)
+    A = solver.plan(prob).bind()
+    om, al = _mode1(prob, A)
+    lam, M = A.init_lambda()
+    lam_g, M_g = lam.clone(), M.clone()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = A.graph(lam_g, M_g, om, al, iters=2, stream=stream)   # a mode-1 iteration loop
+    torch.cuda.synchronize()
+    A.sum_M(M)
+    A.sweep(lam, M, forward=True, costs_out=True)
+    A.sum_M(M)
+    g.replay()                                                    # rewrites the handed-on costs
+    with pytest.raises(_lib.DgError) as e:
+        A.sweep(lam, M, forward=False, costs_in=True)
+    assert "DG_SWEEP_COSTS_IN" in str(e.value)
+    with pytest.raises(_lib.DgError) as e:                        # its averaging terms are mode 1 now
+        A.sweep(lam, M, forward=False)
+    assert "mode" in str(e.value)
+    A.sum_M(M)
+    A.sweep(lam, M, forward=False)
+    torch.cuda.synchronize()
+    assert torch.isfinite(lam).all()
