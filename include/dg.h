@@ -287,7 +287,7 @@ size_t dg_backward_workspace_bytes(const dg_arena* arena, int32_t iters, int32_t
  * respect to the final (lam, M).  Outputs g_lam0, g_M0, g_omega, g_alpha
  * (arena order; g_omega / g_alpha accumulate over all blocks as in Alg. 2,
  * for mode 0 they are the gradients of the per-slot values the scalar
- * expands to).  The forward pass is recomputed from checkpoints of (lam, M)
+ * expands to; either may be NULL, and is then not computed).  The forward pass is recomputed from checkpoints of (lam, M)
  * kept every ckpt_every iterations in workspace; each segment between two
  * checkpoints is re-run as recording sweeps whose argmins (per node and per
  * slot) the adjoint sweeps then read back.  opts->renorm_every must be 0 (the

@@ -883,7 +883,7 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
                         void* workspace, size_t ws_bytes, const dg_options* opts) {
   const bool have_ckpt = lam0 == nullptr;
   if (dg_status s = check_state(ar)) return s;
-  if ((!have_ckpt && !M0) || !g_lam_T || !g_M_T || !g_lam0 || !g_M0 || !g_omega || !g_alpha)
+  if ((!have_ckpt && !M0) || !g_lam_T || !g_M_T || !g_lam0 || !g_M0)
     return fail(DG_EINVAL, "dg_backward: null pointer");
   if (mode != 0 && mode != 1) return fail(DG_EINVAL, "dg_backward: mode must be 0 or 1");
   if (mode == 1 && (!omega || !alpha)) return fail(DG_EINVAL, "dg_backward: mode 1 needs omega and alpha");
@@ -910,8 +910,8 @@ dg_status backward_impl(dg_arena* ar, void* stream, const float* lam0, const flo
   auto cpy = [&](void* d, const void* src, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, st);
   };
-  e = cudaMemsetAsync(g_omega, 0, bNS, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g_alpha, 0, bNS, st);
+  if (g_omega) e = cudaMemsetAsync(g_omega, 0, bNS, st);
+  if (e == cudaSuccess && g_alpha) e = cudaMemsetAsync(g_alpha, 0, bNS, st);
   if (iters == 0) {
     cpy(g_lam0, g_lam_T, bNS);
     cpy(g_M0, g_M_T, bNS);

@@ -101,8 +101,8 @@ struct AdjArgs {
   // weights of mode 0); the long BDDs use the per-variable arrays above
   const float2* slot_in;
   float* g_lam;            // in: gradient of lambda after the sweep; out: before
-  float* g_omega;          // accumulated
-  float* g_alpha;          // accumulated
+  float* g_omega;          // accumulated (nullable: not computed)
+  float* g_alpha;          // accumulated (nullable: not computed)
   float* sdot;             // out: alpha * (gradient of lambda after the sweep), per slot
   // long BDDs: the records of the sweep and per-node gradient scratch of
   // SP(., T) and SP(r, .)

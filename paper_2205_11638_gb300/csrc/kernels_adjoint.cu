@@ -84,8 +84,8 @@ __device__ __forceinline__ LevelIn load_level(const DevArena& A, const AdjArgs& 
   r.om = MODE == 1 ? a.omega[sb + q] : a.omega0;
   const float seed = a.seed_M ? a.seed_M[sb + q] : 0.0f;
   r.md = seed + in.x;  // gradient of M^new
-  r.ga = a.g_alpha[sb + q];
-  r.go = a.g_omega[sb + q];
+  r.ga = a.g_alpha ? a.g_alpha[sb + q] : 0.0f;
+  r.go = a.g_omega ? a.g_omega[sb + q] : 0.0f;
   return r;
 }
 
@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(128) k_adjoint(DevArena A, AdjArgs a, int regi
     const float g = s.gl[q];
     const float Mt = in.md - g;
     a.sdot[sb + q] = in.al * g;                              // contribution to S-dot
-    a.g_alpha[sb + q] = in.ga + g * in.S;
-    a.g_omega[sb + q] = in.go + Mt * in.diff;
+    if (a.g_alpha) a.g_alpha[sb + q] = in.ga + g * in.S;
+    if (a.g_omega) a.g_omega[sb + q] = in.go + Mt * in.diff;
     const float dm1 = in.om * Mt, dm0 = -in.om * Mt;
     s.gl[q] = g + dm1;                                       // gradient of lambda^old
     const int v0 = in.amin & 0xFFu, v1 = in.amin >> 8;

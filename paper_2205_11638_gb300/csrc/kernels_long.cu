@@ -430,8 +430,8 @@ __global__ void __launch_bounds__(128) k_long_adjoint(DevArena A, AdjArgs a) {
     if (lane == 0) {
       const int2 am = a.rec_lamin[q - A.long_slot_base];
       a.sdot[q] = al * g;
-      a.g_alpha[q] = a.g_alpha[q] + g * S;
-      a.g_omega[q] = a.g_omega[q] + Mt * a.rec_diff[q];
+      if (a.g_alpha) a.g_alpha[q] = a.g_alpha[q] + g * S;
+      if (a.g_omega) a.g_omega[q] = a.g_omega[q] + Mt * a.rec_diff[q];
       a.g_lam[q] = g + dm1;
       A2[am.x] += dm0;
       A1[c.code[am.x].x] += dm0;  // terminals absorb into their unused entries

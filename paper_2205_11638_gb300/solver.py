@@ -384,10 +384,12 @@ class DualIterate(torch.autograd.Function):
         A = ctx.arena
         g_lam = A.zeros() if g_lam is None else g_lam.contiguous().float()
         g_M = A.zeros() if g_M is None else g_M.contiguous().float()
-        gl0, gM0, gw, ga = A.backward_checkpointed(om, al, ctx.iters, ctx.ckpt, g_lam, g_M, ctx.workspace)
+        # the per-slot parameter gradients only when autograd wants them
+        need_w = ctx.has_params and ctx.needs_input_grad[2]
+        need_a = ctx.has_params and ctx.needs_input_grad[3]
+        outs = [A.zeros(), A.zeros(), A.zeros() if need_w else None, A.zeros() if need_a else None]
+        gl0, gM0, gw, ga = A.backward_checkpointed(om, al, ctx.iters, ctx.ckpt, g_lam, g_M, ctx.workspace, outs=outs)
         ctx.workspace = None
-        if not ctx.has_params:
-            gw = ga = None
         return gl0, gM0, gw, ga, None, None, None
 
 

@@ -119,6 +119,26 @@ def test_checkpoint_interval_does_not_change_gradients():
             assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("with_long", [False, True])
+def test_parameter_gradients_are_optional(with_long):
+    # g_omega / g_alpha may be NULL: not computed, the other gradients unchanged
+    prob = workloads.long_rows_mix(seed=41) if with_long else workloads.matching_quadratic(L=40, R=40, pairs=1600, seed=6)
+    A = solver.plan(prob).bind()
+    lam, M = A.init_lambda()
+    rng = np.random.default_rng(1)
+    nl = A.plan.sizes.num_lambda
+    gl, gM = A.from_csr(rng.normal(size=nl)), A.from_csr(rng.normal(size=nl))
+    om = A.from_csr(rng.uniform(0.2, 0.8, size=nl))
+    al = A.from_csr(np.full(nl, 0.5))
+    full = A.backward(lam, M, om, al, 4, 2, gl, gM)
+    for keep in ((0, 1), (0, 1, 2), (0, 1, 3)):
+        outs = [A.zeros() if k in keep else None for k in range(4)]
+        A.backward_into(lam, M, om, al, 4, 2, gl, gM, outs)
+        torch.cuda.synchronize()
+        for k in keep:
+            assert torch.equal(outs[k], full[k])
+
+
 def test_config3_matching_20_unrolled_iterations_lb_loss():
     """Matching with linearised quadratic terms, per-slot omega (sigmoid) and
     alpha (softmax per variable), 20 unrolled iterations, gradient of the
