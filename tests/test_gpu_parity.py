@@ -79,6 +79,19 @@ def test_config2_independent_set_parity():
     _check_iterations(workloads.independent_set(), 1, 200)
 
 
+@pytest.mark.parametrize("per_slot", [False, True])
+def test_variables_with_many_slots(per_slot):
+    # every variable in more than 32 rows: S and the per-slot terms come from
+    # the warp-per-variable reduction
+    prob = workloads.independent_set(n=800, avg_deg=48.0, seed=7)
+    if not per_slot:
+        _check_iterations(prob, 1, 60)
+        return
+    rng = np.random.default_rng(8)
+    omega = rng.uniform(0.2, 0.8, size=len(prob["col"]))
+    _check_iterations(prob, 1, 60, omega=omega, alpha=_softmax_alpha(prob["col"], prob["n"], rng))
+
+
 def test_config3_matching_per_slot_parameters():
     prob = workloads.matching_quadratic()
     rng = np.random.default_rng(3)

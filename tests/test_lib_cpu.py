@@ -230,7 +230,8 @@ def test_calls_on_missing_arena_fail_cleanly():
 @pytest.mark.parametrize("make", [lambda: workloads.set_cover(), lambda: workloads.independent_set(n=1500, seed=4),
                                   lambda: workloads.matching_quadratic(L=30, R=30, pairs=900, seed=5),
                                   lambda: workloads.tracking(frames=6, dets=200, seed=6),
-                                  lambda: workloads.batched_mix(num=6, scale=0.03)[0]])
+                                  lambda: workloads.batched_mix(num=6, scale=0.03)[0],
+                                  lambda: workloads.independent_set(n=800, avg_deg=48.0, seed=7)])
 def test_plans_pass_the_validator(make):
     """Every plan the builder makes satisfies the arena invariants the kernels
     rely on (dg_plan_validate), also under non-default layout options."""
@@ -253,7 +254,7 @@ def test_validator_catches_each_corruption(tmp_path):
     out = subprocess.check_output([str(exe)], text=True).strip().splitlines()
     res = {ln.split("|")[0]: (int(ln.split("|")[1]), ln.split("|", 2)[2]) for ln in out}
     assert res.pop("intact") == (0, "")
-    assert len(res) == 10
+    assert len(res) == 11
     for name, (st, msg) in res.items():
         assert st == _lib.DG_EINVAL and msg.startswith("dg_plan_validate:"), (name, st, msg)
 

@@ -75,5 +75,6 @@ int main() {
   run("group_shared_memory", [](Plan& Q) { Q.groups[0].region_bytes = 0; });
   run("bound_chunk_gap", [](Plan& Q) { Q.lb_chunks[3] -= 1; });
   run("tile_bases", [](Plan& Q) { Q.tiles[0].slot_base = kWarp; });
+  run("wide_variable_list", [](Plan& Q) { Q.wide_vars.push_back(0); });
   return 0;
 }
