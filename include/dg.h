@@ -91,7 +91,13 @@ typedef struct dg_options {
   int32_t group_ratio_pct; /* a launch group keeps tiles whose shared-memory
                               footprint is at least this percent of its largest
                               (default 85) */
-  int32_t reserved[5];
+  int32_t long_lanes;    /* lanes given to each long BDD whose levels have at
+                            most 32 nodes in the plain sweeps: 1, 2, 4, 8, 16
+                            or 32, raised to the widest such level's power of
+                            two (default: chosen by dg_bind, at least four
+                            warps per SM); any other value fails dg_plan with
+                            DG_EINVAL */
+  int32_t reserved[4];
 } dg_options;
 
 typedef struct dg_sizes {

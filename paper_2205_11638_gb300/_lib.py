@@ -35,7 +35,7 @@ class dg_options(ctypes.Structure):
     _fields_ = [("tile_nodes", c_int32), ("tile_slots", c_int32), ("block_threads", c_int32),
                 ("renorm_every", c_int32), ("omega", c_float), ("num_threads", c_int32),
                 ("host_mb_limit", c_int32), ("chunk_rows", c_int32), ("group_ratio_pct", c_int32),
-                ("reserved", c_int32 * 5)]
+                ("long_lanes", c_int32), ("reserved", c_int32 * 4)]
 
 
 class dg_sizes(ctypes.Structure):

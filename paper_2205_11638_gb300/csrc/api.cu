@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libdg (declared in include/dg.h): status codes,
 // two-phase build (host plan, device bind), the solver calls, the CUDA graph
 // of the iteration loop.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -309,6 +310,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   cp(P.off.long_lvl, P.long_lvl.data(), P.long_lvl.size() * 4);
   cp(P.off.long_in_ptr, P.long_in_ptr.data(), P.long_in_ptr.size() * 4);
   cp(P.off.long_in, P.long_in.data(), P.long_in.size() * 4);
+  cp(P.off.long_order, P.long_order.data(), P.long_order.size() * 4);
   cudaError_t e = cudaMemcpyAsync(arena_dev, h.data(), image, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)arena_dev + P.off.S, 0, P.off.total - P.off.S, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -367,6 +369,7 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.long_lvl = (const int32_t*)(b + P.off.long_lvl);
   A.long_in_ptr = (const int32_t*)(b + P.off.long_in_ptr);
   A.long_in = (const int32_t*)(b + P.off.long_in);
+  A.long_order = (const int32_t*)(b + P.off.long_order);
   A.long_d = (float*)(b + P.off.long_d);
   A.long_t = (float*)(b + P.off.long_t);
   A.nodecost = (float*)(b + P.off.nodecost);
@@ -386,6 +389,22 @@ dg_status dg_bind(const dg_plan_t* plan, void* arena_dev, size_t arena_bytes, vo
   A.long_slot_base = P.long_slot_base;
   A.long_cost_size = P.long_cost_size;
   A.long_stream = P.long_stream;
+  A.num_long_narrow = P.num_long_narrow;
+  {
+    // lanes per narrow long BDD: the widest level's power of two (or the
+    // option's, if larger); by default doubled (fewer BDDs per warp) while
+    // that leaves fewer than four warps per SM
+    int G = 1, maxw = 1, sms = 1;
+    for (int32_t i = 0; i < P.num_long_narrow; ++i) maxw = std::max(maxw, P.longs[P.long_order[i]].maxw);
+    while (G < maxw) G <<= 1;
+    if (P.long_lanes > 0) {
+      G = std::max(G, (int)P.long_lanes);
+    } else {
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ar->device);
+      while (G < kWarp && (int64_t)(P.num_long_narrow + kWarp / G - 1) / (kWarp / G) < 4LL * sms) G <<= 1;
+    }
+    A.long_lanes = G;
+  }
   // the per-slot weights of mode 0 the adjoint reads, laid out once
   launch_fill_slot_invdeg(A, st);
   e = cudaStreamSynchronize(st);

@@ -156,6 +156,9 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   const int32_t n = R->n;
   const int64_t m = R->m;
   if (n < 0 || m < 0) return fail(DG_EINVAL, "dg_plan: negative sizes");
+  if (opts && opts->long_lanes != 0 &&
+      (opts->long_lanes < 0 || opts->long_lanes > kWarp || (opts->long_lanes & (opts->long_lanes - 1)) != 0))
+    return fail(DG_EINVAL, "dg_plan: long_lanes must be 0 or a power of two up to 32");
   if (R->row_ptr[0] != 0) return fail(DG_EINVAL, "dg_plan: row_ptr[0] must be 0");
   const int64_t nnz = R->row_ptr[m];
   if (nnz > (int64_t)INT32_MAX / 2) return fail(DG_EINVAL, "dg_plan: too many nonzeros");
@@ -544,6 +547,17 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
     if (cost_base >= (int64_t)INT32_MAX || P.long_in_ptr[num_long_nodes] >= (int64_t)INT32_MAX)
       return fail(DG_EINVAL, "dg_plan: long BDDs exceed 2^31 nodes or arcs");
     P.long_cost_size = (int32_t)cost_base;
+    // the plain sweeps pack the narrow long BDDs several to a warp: list them
+    // first, longest first (a warp's BDDs then take about as many levels)
+    P.long_order.clear();
+    for (size_t b = 0; b < P.longs.size(); ++b)
+      if (P.longs[b].maxw <= kWarp) P.long_order.push_back((int32_t)b);
+    std::stable_sort(P.long_order.begin(), P.long_order.end(),
+                     [&](int32_t x, int32_t y) { return P.longs[x].k > P.longs[y].k; });
+    P.num_long_narrow = (int32_t)P.long_order.size();
+    P.long_lanes = opts ? opts->long_lanes : 0;
+    for (size_t b = 0; b < P.longs.size(); ++b)
+      if (P.longs[b].maxw > kWarp) P.long_order.push_back((int32_t)b);
   }
   const int64_t num_slots = slot_base;
   if (num_slots >= (int64_t)INT32_MAX || node_base >= (int64_t)INT32_MAX)
@@ -622,6 +636,7 @@ dg_status build_plan(const dg_rows* R, const dg_options* opts, Plan& P) {
   P.off.long_lvl = put(P.long_lvl.size() * 4);
   P.off.long_in_ptr = put(P.long_in_ptr.size() * 4);
   P.off.long_in = put(P.long_in.size() * 4);
+  P.off.long_order = put(P.long_order.size() * 4);
   P.off.S = put((size_t)n * 4);
   P.off.Sbar = put((size_t)n * 4);
   P.off.slot_avg = put((size_t)num_slots * 4);
@@ -792,6 +807,19 @@ dg_status validate_plan(const Plan& P) {
     }
     if (lslot != NS || cost_base != P.long_cost_size || code_base != P.sizes.num_long_nodes)
       return bad("long BDDs do not cover the arrays");
+    // the order list: a permutation, the narrow BDDs (levels within a warp) first
+    if (P.long_order.size() != P.longs.size() || P.num_long_narrow < 0 ||
+        P.num_long_narrow > (int32_t)P.longs.size())
+      return bad("long BDD order malformed");
+    if (P.long_lanes < 0 || P.long_lanes > kWarp || (P.long_lanes & (P.long_lanes - 1)) != 0)
+      return bad("lanes per narrow long BDD not a power of two up to 32");
+    std::vector<char> listed(P.longs.size(), 0);
+    for (size_t i = 0; i < P.long_order.size(); ++i) {
+      const int32_t b = P.long_order[i];
+      if (b < 0 || b >= (int32_t)P.longs.size() || listed[b]++) return bad("long BDD order not a permutation");
+      if ((P.longs[b].maxw <= kWarp) != ((int32_t)i < P.num_long_narrow))
+        return bad("long BDD order: narrow and wide BDDs mixed");
+    }
   }
   if (real_slots != NL || real_nodes != P.sizes.num_nodes) return bad("slot or node count mismatch");
   // variables: CSR and ELL columns point back at their own slots, rows ascending

@@ -99,6 +99,9 @@ struct DevArena {
   const int32_t* long_lvl;
   const int32_t* long_in_ptr;  // CSR of in-arcs over own nodes (global index)
   const int32_t* long_in;      // parent node number << 1 | beta
+  // the long BDDs whose levels have at most 32 nodes ("narrow"; longest
+  // first), then the others (ascending): indices into `longs`
+  const int32_t* long_order;
   float* long_d;               // scratch per node of long BDDs: SP(r, .)
   float* long_t;               // ... SP(., T)
   // scratch per node and lane of the tiles (layout of lohi8): SP(r, .) as a
@@ -123,6 +126,8 @@ struct DevArena {
   int32_t long_slot_base;   // first slot of the long BDDs (after every tile's slots)
   int32_t long_cost_size;   // entries of long_d / long_t
   int32_t long_stream;      // stream of the fork/join set the long BDDs run on
+  int32_t num_long_narrow;  // narrow long BDDs (the head of long_order)
+  int32_t long_lanes;       // lanes per narrow BDD in the plain sweeps (a power of two, set at bind)
 };
 
 // Tiles that one kernel launch sweeps: consecutive tiles whose shared-memory
@@ -181,6 +186,9 @@ struct Plan {
   std::vector<LongBdd> longs;
   std::vector<int2> long_code;
   std::vector<int32_t> long_lvl, long_in_ptr, long_in;
+  std::vector<int32_t> long_order;  // see DevArena::long_order
+  int32_t num_long_narrow = 0;
+  int32_t long_lanes = 0;           // dg_options::long_lanes (0: chosen at bind)
   std::vector<int64_t> long_rank_ptr;  // per long BDD, first entry of long_lo / long_hi
   std::vector<int32_t> long_lo, long_hi;  // child ranks as in lo8 / hi8 (-2 bottom, -1 top)
   int32_t long_slot_base = 0, long_cost_size = 0, long_stream = 0;
@@ -188,7 +196,7 @@ struct Plan {
   struct Off {
     size_t tiles, desc, lohi8, slot_var, slot_row, var_ptr, var_slots, var_ell, wide_vars, c, invdeg, inst_row_ptr,
         inst_var_ptr,
-        lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, S, Sbar, slot_avg, E, lb_part,
+        lb_chunks, inst_chunk_ptr, inst_unc, longs, long_code, long_lvl, long_in_ptr, long_in, long_order, S, Sbar, slot_avg, E, lb_part,
         long_d, long_t, nodecost, slot_invdeg, total;
   } off{};
   size_t smem_sweep = 0;   // dynamic smem of the sweep kernels

@@ -100,11 +100,16 @@ __device__ __forceinline__ LongCtx long_ctx(const DevArena& A, int b) {
   return c;
 }
 
-// alpha_ij S_i of slot q (mode 1), S_i / |J_i| (mode 0), from the per-slot
-// terms the S reduction before the sweep wrote
+// lambda^new = lambda - M^new + (alpha_ij S_i in mode 1, S_i / |J_i| in mode
+// 0; the per-slot term the S reduction before the sweep wrote), with every
+// rounding spelled out: M^new = omega (m1 - m0) is rounded on its own (the
+// value stored as M), the mode-1 term enters by one fused multiply-add.  The
+// general level loop and the narrow one (which loads the inputs levels ahead)
+// therefore round alike whatever the compiler would contract.
 template <int MODE>
-__device__ __forceinline__ float long_avg(const DevArena& A, const SweepArgs& a, int64_t q) {
-  return MODE == 1 ? a.alpha[q] * A.slot_avg[q] : A.slot_avg[q];
+__device__ __forceinline__ float long_lambda_new(float l, float Mn, float al, float av) {
+  const float r = l - Mn;
+  return MODE == 1 ? __fmaf_rn(al, av, r) : r + av;
 }
 
 // The records of a recording sweep handed the costs: the choices the
@@ -225,6 +230,225 @@ __device__ __forceinline__ void level_minima(const LongCtx& c, int h, int lane, 
   }
 }
 
+// ---- plain sweeps of narrow long BDDs --------------------------------------
+// A long BDD whose levels all have at most 32 nodes (a long cardinality or
+// assignment row) is swept by a segment of G lanes (G a power of two at least
+// its widest level, 32 / G BDDs to a warp): node lvl[h] + s of level h
+// belongs to the segment's lane s.  The costs of the sweep direction stay in
+// a register, a pull reads a parent's (forward) or a child's (backward) by a
+// shuffle inside the segment, minima are shuffles inside the segment, and
+// what does not change during the sweep (level bounds, child codes, in-arcs,
+// the opposite costs, lambda, omega, alpha, the averaging term) is loaded
+// two levels ahead.  The general loop gives a whole warp to one level and
+// reads every cost back through L2 after the lane that wrote it.  The FP32
+// operations and their order (in-arcs ascending; minima are exact) are the
+// general loop's, so the results are bit-identical; the costs still go to
+// long_d / long_t for the sweep after.  The segments of a warp walk their
+// own BDDs side by side; one whose BDD has fewer levels idles at the end.
+
+// What lane s of a segment needs of one level (node f + s when s < w).
+struct NarrowLevel {
+  int f, w;         // first node number, width (0 outside the BDD's levels)
+  int2 cc;          // children of node f + s (the bottom terminal twice off the level)
+  int i0, deg;      // forward: its in-arcs in[i0 .. i0 + deg)
+  int32_t in0, in1; // ... the first two of them
+  float c0, c1;     // forward: SP(child, T) by the 0- / 1-arc; backward: SP(r, f + s) in c0
+  float l, om, al, av;  // lambda, omega, alpha (mode 1) and the averaging term of the level's slot
+};
+
+// The lanes of one segment: the first lane, the lane within it, its size.
+struct Seg {
+  int base, s, G;
+};
+
+__device__ __forceinline__ float seg_min(float x, int G) {
+  for (int o = G >> 1; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(kFull, x, o));
+  return x;
+}
+
+// First half of a level's loads: its node range and the codes (and, forward,
+// the in-arc range) of node f + s.  L outside 0 .. k - 1 (k the segment's
+// level count, 0 for a segment without a BDD) gives an empty level.  Loads
+// are predicated into the fields (no select waits on them).
+template <bool FWD>
+__device__ __forceinline__ void narrow_nodes(const LongCtx& c, NarrowLevel& r, int L, int f, int e, int s, int k) {
+  r.f = f;
+  r.w = L >= 0 && L < k ? e - f : 0;
+  const bool on = s < r.w;
+  r.cc = make_int2((int)kBotCode, (int)kBotCode);
+  if (on) r.cc = c.code[f + s];
+  if (FWD) {
+    r.i0 = 0;
+    int i1 = 0;
+    if (on) {
+      r.i0 = c.inp[f + s];
+      i1 = c.inp[f + s + 1];
+    }
+    r.deg = i1 - r.i0;
+  } else {
+    r.c0 = f_inf();
+    if (on) r.c0 = c.d[f + s];
+    r.c1 = 0.0f;
+  }
+}
+
+// Second half: what depends on the first (forward: the children's SP(., T),
+// the first two in-arcs) and the level's per-slot inputs (clamped to the
+// BDD's levels; unused outside them).
+template <bool FWD, int MODE>
+__device__ __forceinline__ void narrow_inputs(const DevArena& A, const SweepArgs& a, const LongCtx& c,
+                                              NarrowLevel& r, int L) {
+  if (FWD) {
+    r.in0 = 0;
+    r.in1 = 0;
+    if (r.deg > 0) r.in0 = c.in[r.i0];
+    if (r.deg > 1) r.in1 = c.in[r.i0 + 1];
+    r.c0 = c.t[r.cc.x];
+    r.c1 = c.t[r.cc.y];
+  }
+  const int64_t q = c.B.slot_base + min(max(L, 0), c.B.k - 1);
+  r.l = a.lam[q];
+  r.om = MODE == 1 ? a.omega[q] : a.omega0;
+  r.al = MODE == 1 ? a.alpha[q] : 0.0f;
+  r.av = A.slot_avg[q];
+}
+
+// The update of one level from its minima (the general loop's arithmetic);
+// the segment's lane 0 stores lambda and M when `store`.  Returns lambda^new.
+template <int MODE>
+__device__ __forceinline__ float narrow_update(const SweepArgs& a, const NarrowLevel& r, int64_t q, float x0,
+                                               float x1, int G, bool store) {
+  const float m0 = seg_min(x0, G), m1 = r.l + seg_min(x1, G);
+  const float Mn = __fmul_rn(r.om, m1 - m0);
+  const float ln = long_lambda_new<MODE>(r.l, Mn, r.al, r.av);
+  if (store) {
+    a.lam[q] = ln;
+    a.M[q] = Mn;
+  }
+  return ln;
+}
+
+// Top-down over the levels: with UPD the forward sweep (min-marginals, the
+// update, SP(r, .) under the new lambda; SP(., T) in long_t already), without
+// it SP(r, .) under lambda alone (the first pass of a backward sweep that
+// was not handed the costs).  Leaves SP(r, .) in long_d.  Every load that
+// another load's address depends on is issued two levels before it is
+// needed: while level h is worked on, level h + 2 receives its dependent
+// loads (children's SP(., T), in-arcs, per-slot inputs), level h + 4 its
+// node loads, and the end of level h + 6 is read.  Five level records take
+// turns; the loop is unrolled by five so that they rotate by name (a
+// register copy would wait for the loads in flight).  k: the segment's
+// levels; kmax: the warp's.
+template <int MODE, bool UPD>
+__device__ __forceinline__ void narrow_down(const DevArena& A, const SweepArgs& a, const LongCtx& c, const Seg& g,
+                                            int k, int kmax) {
+  NarrowLevel r0, r1, r2, r3, r4;
+  int st = k > 0 ? c.lvl[0] : 0;
+  int en = k > 0 ? c.lvl[1] : st;  // levels 0 .. 3: node loads, 0 and 1 also the rest
+  narrow_nodes<true>(c, r0, 0, st, en, g.s, k);
+  narrow_inputs<true, MODE>(A, a, c, r0, 0);
+  st = en;
+  en = k > 1 ? c.lvl[2] : st;
+  narrow_nodes<true>(c, r1, 1, st, en, g.s, k);
+  narrow_inputs<true, MODE>(A, a, c, r1, 1);
+  st = en;
+  en = k > 2 ? c.lvl[3] : st;
+  narrow_nodes<true>(c, r2, 2, st, en, g.s, k);
+  st = en;
+  en = k > 3 ? c.lvl[4] : st;
+  narrow_nodes<true>(c, r3, 3, st, en, g.s, k);
+  int eA = k > 4 ? c.lvl[5] : en;  // end of level h + 4
+  int eB = k > 5 ? c.lvl[6] : eA;  // end of level h + 5
+  float dreg = g.s == 0 ? 0.0f : f_inf();  // SP(r, .) of level h (level 0 is the root)
+  if (g.s == 0 && k > 0) c.d[2] = 0.0f;
+  auto level = [&](int h, NarrowLevel& s0, NarrowLevel& s1, NarrowLevel& s2, NarrowLevel& s3, NarrowLevel& s4) {
+    narrow_inputs<true, MODE>(A, a, c, s2, h + 2);
+    narrow_nodes<true>(c, s4, h + 4, s3.f + s3.w, eA, g.s, k);
+    eA = eB;
+    if (h + 7 <= k) eB = c.lvl[h + 7];
+    const int maxdeg = (int)__reduce_max_sync(kFull, (unsigned)s1.deg);
+    const float ln = UPD ? narrow_update<MODE>(a, s0, c.B.slot_base + h, dreg + s0.c0, dreg + s0.c1, g.G,
+                                               g.s == 0 && h < k)
+                         : s0.l;
+    if (h + 1 < kmax) {
+      // SP(r, .) of level h + 1: its in-arcs ascending, each parent's cost from the parent's lane
+      float best = f_inf();
+      for (int j = 0; j < maxdeg; ++j) {
+        const bool has = j < s1.deg;
+        int32_t in = j == 0 ? s1.in0 : s1.in1;
+        if (j >= 2 && has) in = c.in[s1.i0 + j];
+        const float dp = __shfl_sync(kFull, dreg, g.base + (((in >> 1) - s0.f) & (g.G - 1)));
+        if (has) best = fminf(best, (in & 1) ? dp + ln : dp);
+      }
+      const bool on = g.s < s1.w;
+      if (on) c.d[s1.f + g.s] = best;
+      dreg = on ? best : f_inf();
+    }
+  };
+  for (int h = 0; h < kmax; h += 5) {
+    level(h, r0, r1, r2, r3, r4);
+    if (h + 1 < kmax) level(h + 1, r1, r2, r3, r4, r0);
+    if (h + 2 < kmax) level(h + 2, r2, r3, r4, r0, r1);
+    if (h + 3 < kmax) level(h + 3, r3, r4, r0, r1, r2);
+    if (h + 4 < kmax) level(h + 4, r4, r0, r1, r2, r3);
+  }
+}
+
+// Bottom-up over the levels: with UPD the backward sweep (SP(r, .) in long_d
+// already), without it SP(., T) under lambda alone (the first pass of a
+// forward sweep that was not handed the costs).  Leaves SP(., T) in long_t
+// (the terminals' entries are the caller's).  The children's costs come from
+// the lanes of the level below, so only the level bounds feed addresses:
+// while level h is worked on, level h - 3 receives its loads and the start
+// of level h - 5 is read.  Four records take turns (the loop unrolled by
+// four); step t of the warp is level k - 1 - t of each segment.
+template <int MODE, bool UPD>
+__device__ __forceinline__ void narrow_up(const DevArena& A, const SweepArgs& a, const LongCtx& c, const Seg& g,
+                                          int k, int kmax) {
+  NarrowLevel r0, r1, r2, r3;
+  int en = k > 0 ? c.lvl[k] : 0;
+  int st = k > 0 ? c.lvl[k - 1] : en;  // levels k - 1 .. k - 3 loaded before the loop
+  narrow_nodes<false>(c, r0, k - 1, st, en, g.s, k);
+  narrow_inputs<false, MODE>(A, a, c, r0, k - 1);
+  en = st;
+  st = k > 1 ? c.lvl[k - 2] : en;
+  narrow_nodes<false>(c, r1, k - 2, st, en, g.s, k);
+  narrow_inputs<false, MODE>(A, a, c, r1, k - 2);
+  en = st;
+  st = k > 2 ? c.lvl[k - 3] : en;
+  narrow_nodes<false>(c, r2, k - 3, st, en, g.s, k);
+  narrow_inputs<false, MODE>(A, a, c, r2, k - 3);
+  int fA = k > 3 ? c.lvl[k - 4] : st;  // start of level h - 3
+  int fB = k > 4 ? c.lvl[k - 5] : fA;  // start of level h - 4
+  float treg = f_inf();                // SP(., T) of level h + 1 (none below the last level)
+  auto level = [&](int t, NarrowLevel& s0, NarrowLevel& s1, NarrowLevel& s2, NarrowLevel& s3) {
+    const int h = k - 1 - t;  // the segment's level (negative once its BDD is done)
+    narrow_nodes<false>(c, s3, h - 3, fA, s2.f, g.s, k);
+    narrow_inputs<false, MODE>(A, a, c, s3, h - 3);
+    fA = fB;
+    if (h >= 5) fB = c.lvl[h - 5];
+    // the children's SP(., T): level h + 1 from its lanes, the terminals by code
+    const int fn = s0.f + s0.w;
+    float tlo = __shfl_sync(kFull, treg, g.base + ((s0.cc.x - fn) & (g.G - 1)));
+    float thi = __shfl_sync(kFull, treg, g.base + ((s0.cc.y - fn) & (g.G - 1)));
+    if (s0.cc.x < 2) tlo = s0.cc.x == (int)kTopCode ? 0.0f : f_inf();
+    if (s0.cc.y < 2) thi = s0.cc.y == (int)kTopCode ? 0.0f : f_inf();
+    const float ln = UPD ? narrow_update<MODE>(a, s0, c.B.slot_base + h, s0.c0 + tlo, s0.c0 + thi, g.G,
+                                               g.s == 0 && h >= 0)
+                         : s0.l;
+    const float tn = fminf(tlo, ln + thi);
+    const bool on = g.s < s0.w;
+    if (on) c.t[s0.f + g.s] = tn;
+    treg = on ? tn : f_inf();
+  };
+  for (int t = 0; t < kmax; t += 4) {
+    level(t, r0, r1, r2, r3);
+    if (t + 1 < kmax) level(t + 1, r1, r2, r3, r0);
+    if (t + 2 < kmax) level(t + 2, r2, r3, r0, r1);
+    if (t + 3 < kmax) level(t + 3, r3, r0, r1, r2);
+  }
+}
+
 }  // namespace
 
 template <int KIND, int MODE>
@@ -233,8 +457,14 @@ __global__ void __launch_bounds__(128) k_long_sweep(DevArena A, SweepArgs a) {
   constexpr bool FWD = KIND == kFwd || KIND == kFwdRec;
   constexpr bool BWD = KIND == kBwd || KIND == kBwdRec;
   const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= A.num_long) return;  // whole warp leaves
+  int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (KIND == kFwd || KIND == kBwd) {
+    // the plain sweeps take the wide long BDDs here (k_long_narrow the others)
+    if (b >= A.num_long - A.num_long_narrow) return;  // whole warp leaves
+    b = A.long_order[A.num_long_narrow + b];
+  } else if (b >= A.num_long) {
+    return;
+  }
   const LongCtx c = long_ctx(A, b);
   const int64_t sb = c.B.slot_base;
   const int k = c.B.k;
@@ -263,8 +493,8 @@ __global__ void __launch_bounds__(128) k_long_sweep(DevArena A, SweepArgs a) {
         }
       } else {
         const float om = MODE == 1 ? a.omega[q] : a.omega0;
-        const float Mn = om * (m1 - m0);
-        ln = l - Mn + long_avg<MODE>(A, a, q);
+        const float Mn = __fmul_rn(om, m1 - m0);
+        ln = long_lambda_new<MODE>(l, Mn, MODE == 1 ? a.alpha[q] : 0.0f, A.slot_avg[q]);
         if (lane == 0) {
           a.lam[q] = ln;
           a.M[q] = Mn;
@@ -298,8 +528,8 @@ __global__ void __launch_bounds__(128) k_long_sweep(DevArena A, SweepArgs a) {
       const float l = a.lam[q];
       const float m0 = b0, m1 = l + b1;
       const float om = MODE == 1 ? a.omega[q] : a.omega0;
-      const float Mn = om * (m1 - m0);
-      const float ln = l - Mn + long_avg<MODE>(A, a, q);
+      const float Mn = __fmul_rn(om, m1 - m0);
+      const float ln = long_lambda_new<MODE>(l, Mn, MODE == 1 ? a.alpha[q] : 0.0f, A.slot_avg[q]);
       if (lane == 0) {
         a.lam[q] = ln;
         a.M[q] = Mn;
@@ -339,6 +569,51 @@ __global__ void __launch_bounds__(128) k_long_sweep(DevArena A, SweepArgs a) {
     }
   }
   if ((BWD || KIND == kEnergy) && a.E != nullptr && lane == 0) a.E[c.B.row] = c.t[2];  // E^j = SP(r, T)
+}
+
+// Plain forward / backward sweep of the narrow long BDDs (the head of
+// long_order), 32 / G of them to a warp, G = A.long_lanes lanes each (see
+// narrow_down / narrow_up).  A sweep not handed the costs first computes the
+// opposite ones the same way.
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(128) k_long_narrow(DevArena A, SweepArgs a) {
+  constexpr bool FWD = KIND == kFwd;
+  const int lane = threadIdx.x & 31;
+  const int G = A.long_lanes;
+  const int first = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (kWarp / G);
+  if (first >= A.num_long_narrow) return;  // whole warp leaves
+  Seg g;
+  g.s = lane & (G - 1);
+  g.base = lane - g.s;
+  g.G = G;
+  const int i = first + lane / G;
+  const bool act = i < A.num_long_narrow;  // segments past the list sweep nothing
+  const LongCtx c = long_ctx(A, A.long_order[act ? i : first]);
+  const int k = act ? c.B.k : 0;
+  const int kmax = (int)__reduce_max_sync(kFull, (unsigned)k);
+  const bool handed = a.cost_in != nullptr;
+  if (FWD) {
+    if (!handed) {
+      if (g.s == 0 && act) {
+        c.t[kTopCode] = 0.0f;
+        c.t[kBotCode] = f_inf();
+      }
+      narrow_up<MODE, false>(A, a, c, g, k, kmax);
+      __syncwarp();
+    }
+    narrow_down<MODE, true>(A, a, c, g, k, kmax);
+  } else {
+    if (!handed) {
+      narrow_down<MODE, false>(A, a, c, g, k, kmax);
+      __syncwarp();
+    }
+    if (g.s == 0 && act) {
+      c.t[kTopCode] = 0.0f;
+      c.t[kBotCode] = f_inf();
+    }
+    narrow_up<MODE, true>(A, a, c, g, k, kmax);
+    if (a.E != nullptr && g.s == 0 && act) a.E[c.B.row] = c.t[2];  // E^j = SP(r, T), written by this lane
+  }
 }
 
 // Smoothed subproblem (soft-min reading) and its marginals P(x_i = 1):
@@ -525,10 +800,24 @@ int long_grid(const DevArena& A) { return (A.num_long + kLongWarps - 1) / kLongW
 
 template <int KIND>
 void launch_long_kind(const DevArena& A, const SweepArgs& a, cudaStream_t st) {
+  int grid = long_grid(A);
+  if constexpr (KIND == kFwd || KIND == kBwd) {
+    if (A.num_long_narrow > 0) {
+      const int per = kWarp / A.long_lanes;
+      const int warps = (A.num_long_narrow + per - 1) / per;
+      const int ng = (warps + kLongWarps - 1) / kLongWarps;
+      if (a.mode == 1)
+        k_long_narrow<KIND, 1><<<ng, kLongWarps * kWarp, 0, st>>>(A, a);
+      else
+        k_long_narrow<KIND, 0><<<ng, kLongWarps * kWarp, 0, st>>>(A, a);
+    }
+    grid = (A.num_long - A.num_long_narrow + kLongWarps - 1) / kLongWarps;
+    if (grid == 0) return;
+  }
   if (a.mode == 1)
-    k_long_sweep<KIND, 1><<<long_grid(A), kLongWarps * kWarp, 0, st>>>(A, a);
+    k_long_sweep<KIND, 1><<<grid, kLongWarps * kWarp, 0, st>>>(A, a);
   else
-    k_long_sweep<KIND, 0><<<long_grid(A), kLongWarps * kWarp, 0, st>>>(A, a);
+    k_long_sweep<KIND, 0><<<grid, kLongWarps * kWarp, 0, st>>>(A, a);
 }
 
 }  // namespace

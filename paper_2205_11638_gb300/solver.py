@@ -27,8 +27,9 @@ def _ptr(t):
 
 
 def make_options(tile_nodes=0, tile_slots=0, block_threads=0, renorm_every=0, omega=0.0, num_threads=0,
-                 host_mb_limit=0, chunk_rows=0, group_ratio_pct=0):
+                 host_mb_limit=0, chunk_rows=0, group_ratio_pct=0, long_lanes=0):
     o = dg_options()
+    o.long_lanes = int(long_lanes)
     o.host_mb_limit = int(host_mb_limit)
     o.chunk_rows = int(chunk_rows)
     o.group_ratio_pct = int(group_ratio_pct)

@@ -78,10 +78,42 @@ def test_long_rows_only():
     assert A.plan.sizes.num_tiles == 0
 
 
-def test_assignment_instance():
+@pytest.mark.parametrize("lanes", [0, 2])
+def test_assignment_instance(lanes):
     """The assignment workload's shape at 400 x 400 with 300 candidates per
-    left node: 800 rows of about 300 variables, every BDD a long one."""
-    _parity(workloads.assignment(L=400, R=400, cand=300, seed=12), iters_lb=100)
+    left node: 800 rows of about 300 variables, every BDD a long one (swept
+    one to a warp, and 16 to a warp with two lanes each)."""
+    _parity(workloads.assignment(L=400, R=400, cand=300, seed=12), iters_lb=100, long_lanes=lanes)
+
+
+@pytest.mark.parametrize("per_slot", [False, True])
+@pytest.mark.parametrize("name,lanes", [("mix", 0), ("assignment", 0), ("assignment", 2), ("assignment", 8),
+                                        ("mix", 32)])
+def test_plain_sweeps_equal_recording_sweeps(name, lanes, per_slot):
+    """dg_iterate's plain sweeps (the long BDDs whose levels have at most 32
+    nodes swept 32 / G to a warp, G lanes each, path costs in registers)
+    against the recording sweeps of a one-segment dg_iterate_checkpointed
+    (every long BDD through the general level loop, one warp each): lambda,
+    M and the bound bit for bit, at the lane count dg_bind picks and at
+    forced ones (several BDDs of different lengths to a warp)."""
+    if name == "mix":
+        prob = workloads.long_rows_mix(seed=21)
+    else:
+        prob = workloads.assignment(L=120, R=300, cand=280, seed=22)
+    A = solver.plan(prob, long_lanes=lanes).bind()
+    assert A.plan.sizes.num_long_bdds > 0
+    om = al = None
+    if per_slot:
+        rng = np.random.default_rng(5)
+        al = A.from_csr(_softmax_alpha(prob["col"], prob["n"], rng))
+        om = A.from_csr(rng.uniform(0.2, 0.8, size=len(prob["col"])))
+    lam0, M0 = A.init_lambda()
+    T = 6
+    l1, m1 = lam0.clone(), M0.clone()
+    lb1 = A.iterate(l1, m1, om, al, iters=T, lb=True)
+    l2, m2 = lam0.clone(), M0.clone()
+    _, lb2 = A.iterate_checkpointed(l2, m2, om, al, iters=T, ckpt_every=T, lb=True)
+    assert torch.equal(l1, l2) and torch.equal(m1, m2) and torch.equal(lb1, lb2)
 
 
 def test_long_min_marginals_energies_and_seed():

@@ -140,6 +140,14 @@ def test_status_codes():
     with pytest.raises(_lib.DgError) as e:
         solver.plan(empty)
     assert e.value.status == _lib.DG_EINVAL
+    # lanes per narrow long BDD: 0 or a power of two up to 32
+    ok = workloads.single_rows_problem([(np.array([0, 1]), np.array([1, 1]), 0, 1)], 2, np.zeros(2))
+    for lanes in (3, 64, -2):
+        with pytest.raises(_lib.DgError) as e:
+            solver.plan(ok, long_lanes=lanes)
+        assert e.value.status == _lib.DG_EINVAL and "long_lanes" in str(e.value)
+    for lanes in (0, 1, 8, 32):
+        solver.plan(ok, long_lanes=lanes).validate()
 
 
 def _bit_exact(prob):
@@ -254,7 +262,7 @@ def test_validator_catches_each_corruption(tmp_path):
     out = subprocess.check_output([str(exe)], text=True).strip().splitlines()
     res = {ln.split("|")[0]: (int(ln.split("|")[1]), ln.split("|", 2)[2]) for ln in out}
     assert res.pop("intact") == (0, "")
-    assert len(res) == 11
+    assert len(res) == 12
     for name, (st, msg) in res.items():
         assert st == _lib.DG_EINVAL and msg.startswith("dg_plan_validate:"), (name, st, msg)
 

@@ -76,5 +76,6 @@ int main() {
   run("bound_chunk_gap", [](Plan& Q) { Q.lb_chunks[3] -= 1; });
   run("tile_bases", [](Plan& Q) { Q.tiles[0].slot_base = kWarp; });
   run("wide_variable_list", [](Plan& Q) { Q.wide_vars.push_back(0); });
+  run("long_bdd_order", [](Plan& Q) { Q.long_order.push_back(0); });
   return 0;
 }
