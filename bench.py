@@ -413,9 +413,10 @@ def _independent_set_measurement(solver, torch, iters=200, reps=5):
 def _long_rows_measurement(solver, torch, iters=50, reps=3):
     """Sparse assignment with long rows (2,000 x 2,000, 300 candidates per
     left node: 4,000 rows of about 300 variables, every BDD beyond a tile
-    lane): the one-warp-per-BDD sweeps.  Arc updates per second over a
-    CUDA-graph replay of 50 iterations, and the roofline of the long-BDD
-    sweep kernel from its own CUDA-event time."""
+    lane, every level two nodes wide): the plain sweeps of narrow long BDDs,
+    several to a warp.  Arc updates per second over a CUDA-graph replay of
+    50 iterations, and the roofline of the long-BDD sweep kernel from its
+    own CUDA-event time."""
     prob = workloads.assignment()
     A = solver.plan(prob).bind()
     st = A.stats
@@ -459,7 +460,7 @@ def _long_rows_measurement(solver, torch, iters=50, reps=3):
             "N_lambda": int(Nl), "N_v": int(Nv), "long_bdds": int(st.sizes.num_long_bdds),
             "long_nodes": int(st.sizes.num_long_nodes), "iterations": iters,
             "value": 4 * Nv * iters / (t * 1e-3), "unit": UNIT, "ms_per_iteration": t / iters,
-            "roofline": {"bound": "hbm", "kernel": "k_long_sweep (forward and backward)",
+            "roofline": {"bound": "hbm", "kernel": "k_long_narrow (forward and backward; long BDDs of narrow levels, several to a warp)",
                          "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": sweep_ms,
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src},

@@ -18,6 +18,13 @@
 // so a sweep handed the costs (SweepArgs::cost_in, set when the tiles' costs
 // are handed on) skips its first pass: they are already in place.
 //
+// The plain forward and backward sweeps of the long BDDs whose levels have
+// at most 32 nodes (long cardinality and assignment rows) run in
+// k_long_narrow instead: several such BDDs to a warp, G lanes each, the
+// costs of the sweep direction in registers (see narrow_down / narrow_up).
+// The recording sweeps, energies, seeds, min-marginals, smoothed
+// subproblems and adjoints keep one warp per BDD.
+//
 // The arithmetic is the lane kernels': the same FP32 operations per arc;
 // minima are exact, so values do not depend on the order of the reduction;
 // argmins follow the same tie rules (smallest node number for the
