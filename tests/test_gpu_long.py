@@ -87,15 +87,16 @@ def test_assignment_instance(lanes):
 
 
 @pytest.mark.parametrize("per_slot", [False, True])
-@pytest.mark.parametrize("name,lanes", [("mix", 0), ("assignment", 0), ("assignment", 2), ("assignment", 8),
-                                        ("mix", 32)])
+@pytest.mark.parametrize("name,lanes", [("mix", 0), ("assignment", 0), ("assignment", 2), ("assignment", 8)])
 def test_plain_sweeps_equal_recording_sweeps(name, lanes, per_slot):
     """dg_iterate's plain sweeps (the long BDDs whose levels have at most 32
     nodes swept 32 / G to a warp, G lanes each, path costs in registers)
     against the recording sweeps of a one-segment dg_iterate_checkpointed
     (every long BDD through the general level loop, one warp each): lambda,
-    M and the bound bit for bit, at the lane count dg_bind picks and at
-    forced ones (several BDDs of different lengths to a warp)."""
+    M and the bound bit for bit, at the lane count dg_bind picks (32 for
+    both instances: the mix's widest narrow level has 26 nodes, and the
+    assignment instance has too few BDDs to fill the SMs at fewer lanes) and
+    at forced ones (several BDDs of different lengths to a warp)."""
     if name == "mix":
         prob = workloads.long_rows_mix(seed=21)
     else:
