@@ -47,8 +47,10 @@ WORKLOADS = {
 
 
 
-# footprint ratios (percent) of the launch groups the layout tuner tries
-TUNE_RATIOS = (80, 85, 88, 90, 92)
+# layout knobs the tuner tries: locality chunks (rows) and footprint ratios
+# (percent) of the launch groups
+TUNE_CHUNKS = (16384, 32768)
+TUNE_RATIOS = (85, 88, 90, 92)
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -714,13 +716,14 @@ def run_ours(args):
     tuned_ms = None
     layout = None
     if not args.no_tune:
-        # untimed set-up: the launch groups' footprint ratio (a layout knob:
-        # how tiles are grouped into launches, never the arithmetic) chosen
-        # among a few by timing whole sweep pairs, then the launch shapes
+        # untimed set-up: the locality chunk and the launch groups' footprint
+        # ratio (layout knobs: how rows are ordered into tiles and tiles into
+        # launches, never the arithmetic) chosen among a few by timing whole
+        # sweep pairs, then the launch shapes
         from paper_2205_11638_gb300 import autotune
         t1 = time.perf_counter()
         del A, plan
-        layout, A = autotune.tune(prob, reps=3, chunks=(16384,), ratios=TUNE_RATIOS, use_cache=False,
+        layout, A = autotune.tune(prob, reps=3, chunks=TUNE_CHUNKS, ratios=TUNE_RATIOS, use_cache=False,
                                   block_threads=args.threads, tile_nodes=args.tile_nodes,
                                   tile_slots=args.tile_slots)
         tuned_ms = autotune.tune_launch(A, reps=3)
