@@ -63,7 +63,7 @@ def test_independent_set_row_closed_form():
         assert m0[0] == min(0.0, lam[1]) and m0[1] == min(0.0, lam[0])
 
 
-@pytest.mark.parametrize("k", [2, 3, 5, 8])
+@pytest.mark.parametrize("k", [2, 3, 5, 8, 300])
 def test_at_most_one_closed_form(k):
     """sum x <= 1: m1_i = lam_i, m0_i = min(0, min_{p != i} lam_p)."""
     P = oracle.Oracle(workloads.single_rows_problem([(np.arange(k), np.ones(k), 0, 1)], k, np.zeros(k)))
@@ -77,7 +77,7 @@ def test_at_most_one_closed_form(k):
             assert abs(m0[i] - min(0.0, others.min())) < 1e-15
 
 
-@pytest.mark.parametrize("k", [2, 3, 6, 9])
+@pytest.mark.parametrize("k", [2, 3, 6, 9, 300])
 def test_at_least_one_closed_form(k):
     """sum x >= 1: m1_i = lam_i + sum_{p!=i} min(0, lam_p);
     m0_i = sum_{p!=i} min(0, lam_p) + (min_{p!=i} lam_p if no lam_p < 0 else 0)."""
@@ -139,3 +139,31 @@ def test_minimiser_tie_rules():
             else:
                 want[h] = 1
             np.testing.assert_array_equal(x, want)
+
+
+def _smallest(v, r, negative_only):
+    """Sum of the r smallest entries of v (only the negative ones among them
+    when negative_only)."""
+    w = np.sort(v)[:r]
+    return float(np.minimum(w, 0.0).sum() if negative_only else w.sum())
+
+
+@pytest.mark.parametrize("k,sense,b", [(40, workloads.LE, 3), (500, workloads.LE, 10), (300, workloads.EQ, 25),
+                                       (64, workloads.EQ, 1)])
+def test_cardinality_closed_form(k, sense, b):
+    """Long cardinality rows (the sizes the long-BDD path runs): for sum x <= b
+    the cheapest assignment takes the at most b most negative costs, so
+    m1_i = lam_i + (b - 1 smallest negatives of the others), m0_i = (b
+    smallest negatives of the others); for sum x = b exactly b are taken:
+    m1_i = lam_i + (b - 1 smallest of the others), m0_i = (b smallest of the
+    others)."""
+    P = oracle.Oracle(workloads.single_rows_problem([(np.arange(k), np.ones(k), sense, b)], k, np.zeros(k)))
+    rng = np.random.default_rng(7 * k + b)
+    neg_only = sense == workloads.LE
+    for _ in range(3):
+        lam = rng.normal(size=k)
+        m0, m1 = P.min_marginals(lam)
+        for i in range(0, k, max(1, k // 40)):
+            o = np.delete(lam, i)
+            assert abs(m1[i] - (lam[i] + _smallest(o, b - 1, neg_only))) < 1e-12
+            assert abs(m0[i] - _smallest(o, b, neg_only)) < 1e-12
