@@ -33,7 +33,8 @@ def _random_feasible_problem(seed, n=16, rows=14, kmax=7):
 
 
 @pytest.mark.parametrize("make", [lambda: workloads.set_cover(), lambda: _random_feasible_problem(3),
-                                  lambda: workloads.independent_set(n=300, seed=9)])
+                                  lambda: workloads.independent_set(n=300, seed=9),
+                                  lambda: workloads.long_rows_mix(seed=3, n_short=20)])
 def test_prop1_feasibility_and_monotone_per_sweep(make):
     """Prop. 1: sum_j (lambda_ij + M_ij) = c_i after every sweep (reading of the
     garbled invariant in its proof) and the bound never decreases."""
@@ -94,6 +95,27 @@ def test_single_row_bound():
             continue
         opt, _ = brute.problem_opt(prob)
         assert abs(P.lower_bound(*P.init_lambda()) - opt) < 1e-12
+
+
+@pytest.mark.parametrize("k,sense,b", [(300, workloads.LE, 1), (500, workloads.LE, 10), (300, workloads.EQ, 25),
+                                       (300, workloads.GE, 1)])
+def test_single_long_row_bound(k, sense, b):
+    """One cardinality row over hundreds of variables (a long BDD): the bound
+    at the uniform split is the row's optimum, which sorting gives: the b
+    smallest costs for sum x = b, the at most b negative ones among the b
+    smallest for sum x <= b, and for sum x >= 1 every negative cost or, if
+    there is none, the smallest one."""
+    rng = np.random.default_rng(k + b)
+    c = rng.normal(size=k)
+    P = oracle.Oracle(workloads.single_rows_problem([(np.arange(k), np.ones(k), sense, b)], k, c))
+    w = np.sort(c)
+    if sense == workloads.EQ:
+        opt = w[:b].sum()
+    elif sense == workloads.LE:
+        opt = np.minimum(w[:b], 0.0).sum()
+    else:
+        opt = np.minimum(c, 0.0).sum() if (c < 0).any() else w[0]
+    assert abs(P.lower_bound(*P.init_lambda()) - opt) < 1e-12
 
 
 def test_omega_zero_is_identity():
