@@ -195,3 +195,18 @@ def test_lb_seed_is_minimiser():
     S = np.zeros(P.n)
     np.add.at(S, P.col, M)
     np.testing.assert_array_equal(gM, (S[P.col] < 0).astype(float))
+
+
+def test_openmp_build_is_bit_identical():
+    """The oracle built with OpenMP (sweeps over the BDDs in parallel, the S
+    sums afterwards in the fixed order) gives the single-threaded oracle's
+    lambda, M and bound bit for bit; it only times the all-cores baseline."""
+    prob = workloads.tracking(frames=4, dets=300, seed=17)
+    P1 = oracle.Oracle(prob)
+    P2 = oracle.Oracle(prob, openmp=True)
+    l1, m1 = P1.init_lambda()
+    l2, m2 = P2.init_lambda()
+    l1, m1 = P1.iterate(l1, m1, 0.5, None, 5)
+    l2, m2 = P2.iterate(l2, m2, 0.5, None, 5)
+    assert np.array_equal(l1, l2) and np.array_equal(m1, m2)
+    assert P1.lower_bound(l1, m1) == P2.lower_bound(l2, m2)
