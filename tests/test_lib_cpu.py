@@ -239,7 +239,8 @@ def test_calls_on_missing_arena_fail_cleanly():
                                   lambda: workloads.matching_quadratic(L=30, R=30, pairs=900, seed=5),
                                   lambda: workloads.tracking(frames=6, dets=200, seed=6),
                                   lambda: workloads.batched_mix(num=6, scale=0.03)[0],
-                                  lambda: workloads.independent_set(n=800, avg_deg=48.0, seed=7)])
+                                  lambda: workloads.independent_set(n=800, avg_deg=48.0, seed=7),
+                                  lambda: workloads.assignment(L=60, R=300, cand=260, seed=8)])
 def test_plans_pass_the_validator(make):
     """Every plan the builder makes satisfies the arena invariants the kernels
     rely on (dg_plan_validate), also under non-default layout options."""
